@@ -1,0 +1,68 @@
+"""The whole pCGMG solve, wired from the oracle's pieces (test infrastructure only).
+
+Paper passages: Alg. 2 (PCG) preconditioned by one V-cycle of Alg. 1 on the
+Q4 system of Eqs. 5-9; compliance and sensitivities after it (Eq. 6, Sec. 4).
+Also the plain definition it must agree with: u = K_ff^-1 f_f.
+"""
+
+import numpy as np
+
+from . import fem, multigrid, pcg, sensitivity
+
+
+def solve_direct(nelx, nely, x, E_phase, penal, f, nu=0.3, fixed_edges=fem.BOTTOM):
+    """u = K_ff^-1 f_f by a sparse direct solve; returns u as [nely+1][nelx+1][2]."""
+    E = fem.simp_moduli(x, E_phase, penal)
+    KE = fem.element_stiffness(nu)
+    K = fem.assemble(nelx, nely, E, KE)
+    free = fem.free_dofs(nelx, nely, fixed_edges)
+    return fem.direct_solve(K, f, free).reshape(nely + 1, nelx + 1, 2)
+
+
+def solve_pcgmg(nelx, nely, x, E_phase, penal, f, nu=0.3, fixed_edges=fem.BOTTOM,
+                n_coarsen=3, omega=0.6, nu1=2, nu2=2, tol=1e-10, max_it=1000,
+                coarse_kind="galerkin", u0=None, flexible=False, rr_every=0,
+                vcycle_E=None):
+    """PCG (Alg. 2) with a V-cycle (Alg. 1) preconditioner.
+
+    vcycle_E, when given, replaces the element moduli inside the preconditioner
+    only (the mixed-precision path builds its V-cycle from bfloat16 moduli while
+    the outer operator keeps the float64 ones).
+
+    Returns a dict: u ([nely+1][nelx+1][2], zero on clamped DOFs), iters,
+    converged, history (||r||/||f|| per iteration), E, KE, levels.
+    """
+    E = fem.simp_moduli(x, E_phase, penal)
+    KE = fem.element_stiffness(nu)
+    E_pre = E if vcycle_E is None else np.asarray(vcycle_E, dtype=np.float64)
+    levels = multigrid.build_hierarchy(nelx, nely, E_pre, KE, fixed_edges, n_coarsen, coarse_kind)
+    free = levels[-1].free
+    if vcycle_E is None:
+        K = levels[-1].K
+    else:
+        K = fem.assemble(nelx, nely, E, KE)[free][:, free]
+    f_full = np.asarray(f, dtype=np.float64).ravel()
+    x0 = None if u0 is None else np.asarray(u0, dtype=np.float64).ravel()[free]
+    M = multigrid.vcycle_preconditioner(levels, omega, nu1, nu2)
+    uf, iters, conv, hist = pcg.pcg(lambda v: K @ v, f_full[free], M, x0=x0, tol=tol,
+                                    max_it=max_it, flexible=flexible, rr_every=rr_every)
+    u = np.zeros_like(f_full)
+    u[free] = uf
+    return dict(u=u.reshape(nely + 1, nelx + 1, 2), iters=iters, converged=conv,
+                history=hist, E=E, KE=KE, levels=levels)
+
+
+def compliance_and_gradient(nelx, nely, x, E_phase, penal, f, u, nu=0.3):
+    """C = f.u and dC/dx [n_phase][nely][nelx] for one load case."""
+    KE = fem.element_stiffness(nu)
+    w = sensitivity.element_energy(nelx, nely, KE, u)
+    return sensitivity.compliance(f, u), sensitivity.compliance_gradient(x, E_phase, penal, w)
+
+
+def true_relative_residual(nelx, nely, E, f, u, nu=0.3, fixed_edges=fem.BOTTOM):
+    """||f - K u|| / ||f|| over the free DOFs, by the element-by-element product."""
+    KE = fem.element_stiffness(nu)
+    free = fem.free_dofs(nelx, nely, fixed_edges)
+    r = np.asarray(f, dtype=np.float64).ravel() - fem.apply_K(nelx, nely, E, KE, u)
+    fn = np.linalg.norm(np.asarray(f, dtype=np.float64).ravel()[free])
+    return float(np.linalg.norm(r[free]) / fn)

@@ -1,0 +1,72 @@
+"""Counter-based design generator and square-wall load cases.
+
+Design fractions: per element, the n_phase fractions are a Dirichlet(1,...,1)
+draw built from normalised Exp(1) variates.  Every variate comes from a
+counter-based generator, so the same (seed, mesh, n_phase) gives the same
+design in any language:
+
+    u(e, i) = ((splitmix64(seed XOR (e*n_phase + i)) >> 11) + 1) * 2**-53
+    g(e, i) = -log(u(e, i))
+    x(e, i) = g(e, i) / sum_k g(e, k)
+
+splitmix64 is the output function of Steele, Lea and Flood's SplitMix64
+generator ("Fast splittable pseudorandom number generators", OOPSLA 2014):
+add the golden-ratio increment 0x9E3779B97F4A7C15, then two xor-shift-multiply
+rounds and a final xor-shift.  Applied to a counter it is a stateless hash.
+
+Loads (the square wall, bottom edge clamped):
+  * top-edge case: f_y = -1 at every node of the top edge, corners included;
+  * right-edge case: f_x = +1 at every node of the right edge.  The
+    bottom-right node is clamped, so its load is dropped by the solver.
+"""
+
+import numpy as np
+
+BOTTOM, LEFT, RIGHT, TOP = 1, 2, 4, 8
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(z):
+    """SplitMix64 output function applied to uint64 counters (vectorised)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = z + _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed, counters):
+    """Uniform variates in (0, 1] with 53 random bits, one per counter."""
+    c = np.asarray(counters, dtype=np.uint64) ^ np.uint64(seed)
+    bits = splitmix64(c) >> np.uint64(11)
+    return (bits.astype(np.float64) + 1.0) * 2.0**-53
+
+
+def dirichlet_design(nelx, nely, n_phase, seed, chunk=1 << 22):
+    """Per-element Dirichlet(1,...,1) phase fractions, float64 [n_phase][nely][nelx]."""
+    n_el = nelx * nely
+    out = np.empty((n_phase, n_el), dtype=np.float64)
+    for s in range(0, n_el, chunk):
+        e = np.arange(s, min(n_el, s + chunk), dtype=np.uint64)
+        ctr = e[None, :] * np.uint64(n_phase) + np.arange(n_phase, dtype=np.uint64)[:, None]
+        g = -np.log(uniform01(seed, ctr))
+        out[:, s:s + len(e)] = g / g.sum(axis=0, keepdims=True)
+    return out.reshape(n_phase, nely, nelx)
+
+
+def load_top_edge(nelx, nely, value=-1.0):
+    """f_y = value at every top-edge node; layout [nely+1][nelx+1][2]."""
+    f = np.zeros((nely + 1, nelx + 1, 2), dtype=np.float64)
+    f[nely, :, 1] = value
+    return f
+
+
+def load_right_edge(nelx, nely, value=1.0):
+    """f_x = value at every right-edge node; layout [nely+1][nelx+1][2]."""
+    f = np.zeros((nely + 1, nelx + 1, 2), dtype=np.float64)
+    f[:, nelx, 0] = value
+    return f
