@@ -1,0 +1,165 @@
+/*
+ * libmto -- matrix-free multigrid-preconditioned conjugate gradient (pCGMG)
+ * for the multi-material plane-stress Q4 compliance problem of Luu & Banh,
+ * "A novel preconditioned conjugate gradient multigrid method for
+ * multi-material topology optimization" (arXiv 2301.07457).
+ *
+ * C ABI.  Plain pointers and sizes only.  Every array argument documents
+ * whether it lives on the device ("_dev": memory of the context's CUDA
+ * device) or on the host ("_host").  The caller owns every array it passes;
+ * the library owns the context and everything the context allocates.
+ *
+ * Mesh conventions (the paper's Fig. 3 is missing; these are the library's):
+ *   nelx x nely unit-square elements, element e = j*nelx + i;
+ *   nodes (nelx+1) x (nely+1), node n = j*(nelx+1) + i (x fastest);
+ *   DOF 2n is u_x, 2n+1 is u_y, so nodal vectors are [nely+1][nelx+1][2];
+ *   design fractions are [n_phase][nely][nelx];
+ *   element local nodes run counter-clockwise from the bottom-left.
+ *
+ * Errors: every call returns an mto_status; nothing is thrown across the ABI.
+ * A CUDA failure inside a call returns MTO_ERR_CUDA and leaves the context
+ * in a state where mto_destroy is still valid.
+ *
+ * Streams: all device work of a context is enqueued on the stream given at
+ * creation.  Calls that return statistics to the host synchronise that
+ * stream; all others only enqueue.
+ *
+ * Threads: a context is not thread-safe; use one context per host thread.
+ */
+#ifndef MTO_H
+#define MTO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mto_ctx mto_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  MTO_OK = 0,
+  MTO_ERR_ARG = 1,              /* invalid argument (null pointer, bad size, bad option) */
+  MTO_ERR_UNSUPPORTED_MESH = 2, /* nelx or nely not divisible by 2^n_coarsen, coarsest grid too large */
+  MTO_ERR_OOM = 3,              /* device allocation failed */
+  MTO_ERR_CUDA = 4,             /* a CUDA call failed */
+  MTO_ERR_NOT_CONVERGED = 5,    /* max_it reached; u holds the last iterate */
+  MTO_ERR_BREAKDOWN = 6,        /* p.Kp <= 0, z.r <= 0 or a non-finite scalar in PCG */
+  MTO_ERR_TIMEOUT = 7,          /* a bounded device wait gave up */
+  MTO_ERR_STATE = 8             /* call out of order (e.g. solve before set_design) */
+} mto_status;
+
+/* Clamped edges (both displacement components fixed on every node of the edge). */
+enum { MTO_EDGE_BOTTOM = 1, MTO_EDGE_LEFT = 2, MTO_EDGE_RIGHT = 4, MTO_EDGE_TOP = 8 };
+/* Coarse operators: Galerkin P^T K P (exact), or rediscretised with the mean
+ * of the four child moduli (Sec. 2.1: "obtained from discretization in the
+ * mesh Omega_n"). */
+enum { MTO_COARSE_GALERKIN = 0, MTO_COARSE_REDISCRETIZE = 1 };
+/* FP64: every step in float64.  MIXED: V-cycle in float32 with bfloat16
+ * fine moduli; outer CG vectors, K p, dot products, residual replacement and
+ * the coarsest dense solve in float64. */
+enum { MTO_PRECISION_FP64 = 0, MTO_PRECISION_MIXED = 1 };
+
+typedef struct {
+  double tol;       /* stop when ||f - K u||_2 <= tol * ||f||_2 (recursive residual; Alg. 2) */
+  int max_it;       /* maximum PCG iterations */
+  double omega;     /* damped-Jacobi weight (Sec. 2.3), 0 < omega <= 1 */
+  int nu1, nu2;     /* pre- and post-smoothing sweeps of Alg. 1, each >= 1 */
+  int n_coarsen;    /* number of coarsenings; the V-cycle has n_coarsen+1 grids */
+  int coarse_kind;  /* MTO_COARSE_* */
+  int precision;    /* MTO_PRECISION_* */
+  int rr_every;     /* mixed path: replace r by f - K u every k iterations (0: never) */
+  int flexible;     /* 1: flexible (Polak-Ribiere) beta, 0: Fletcher-Reeves as in Alg. 2 */
+  int check_every;  /* host convergence poll interval in iterations (>= 1) */
+} mto_solver_opts;
+
+typedef struct {
+  int iters;            /* PCG iterations performed (x updates) */
+  int converged;        /* 1 if the stopping rule was met */
+  double rel_res_rec;   /* recursive ||r|| / ||f|| at exit */
+  double rel_res_true;  /* true ||f - K u|| / ||f|| at exit, float64 operator */
+  double ms_setup;      /* device time of the last mto_set_design (ms) */
+  double ms_solve;      /* device time of this mto_solve (ms), all right-hand sides */
+} mto_solve_stats;
+
+/* Fills the defaults: tol 1e-8, max_it 500, omega 0.6, nu1 = nu2 = 2,
+ * n_coarsen 3, Galerkin, FP64, rr_every 25, flexible 0, check_every 4. */
+void mto_default_opts(mto_solver_opts* opts);
+
+/* Creates a context for an nelx x nely mesh with Poisson ratio nu and the
+ * given clamped edges (at least one, so that K_ff is positive definite).
+ * Allocates every device buffer of the level hierarchy (sizes depend only on
+ * the mesh and the options).  device: CUDA ordinal; cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).
+ * Paper: Eq. 6-10 (problem statement), Alg. 1 (grid hierarchy). */
+mto_status mto_create_mesh(mto_ctx** out, int nelx, int nely, double nu, unsigned fixed_edges,
+                           const mto_solver_opts* opts, int device, void* cuda_stream);
+
+/* Sets the design and builds every operator of the hierarchy on the device:
+ * E_e = sum_i x_{e,i}^penal * E_phase[i] (Eq. 5), the fine Jacobi diagonal,
+ * the coarse operators of every level and the coarsest dense inverse.
+ * x_dev: device, float64 [n_phase][nely][nelx], finite values in [0, 1]
+ * (not validated on the device).  E_phase: host, float64 [n_phase], > 0.
+ * n_phase in [1, 16].  penal >= 1. */
+mto_status mto_set_design(mto_ctx* ctx, int n_phase, const double* x_dev, const double* E_phase,
+                          double penal);
+
+/* Solves K u = f for n_rhs load cases by PCG (Alg. 2) preconditioned with one
+ * V-cycle (Alg. 1).  f_dev: device, float64 [n_rhs][nely+1][nelx+1][2];
+ * loads on clamped DOFs are ignored.  u_dev: device, same layout; in: the
+ * warm start (zeros for a cold start), out: the solution, zero on clamped
+ * DOFs.  stats: host, may be NULL (then the call only enqueues work and
+ * returns MTO_OK; the outcome can be read with mto_last_stats).  With stats,
+ * the call synchronises and returns MTO_ERR_NOT_CONVERGED or
+ * MTO_ERR_BREAKDOWN when a right-hand side failed; stats describe the last
+ * right-hand side (iters summed over all). */
+mto_status mto_solve(mto_ctx* ctx, int n_rhs, const double* f_dev, double* u_dev,
+                     mto_solve_stats* stats);
+
+/* Statistics of the last mto_solve (synchronises the context's stream). */
+mto_status mto_last_stats(mto_ctx* ctx, mto_solve_stats* stats);
+
+/* Compliance and sensitivities after a solve (Eq. 6; Sec. 4):
+ * compliance_dev[k] = f_k . u_k (device, float64 [n_rhs]);
+ * dcdx_dev[i][e] = sum_k -penal x_{e,i}^(penal-1) E_i u_{k,e}^T KE u_{k,e}
+ * (device, float64 [n_phase][nely][nelx], may be NULL), using the design of
+ * the last mto_set_design.  f_dev, u_dev as in mto_solve. */
+mto_status mto_compliance_grad(mto_ctx* ctx, int n_rhs, const double* f_dev, const double* u_dev,
+                               double* compliance_dev, double* dcdx_dev);
+
+/* One call with host buffers: copies x and f to the device, runs
+ * set_design + solve (cold start) + compliance/sensitivities, copies u, the
+ * compliances and the sensitivities back.  x_host [n_phase][nely][nelx],
+ * f_host/u_host [n_rhs][nely+1][nelx+1][2], compliance_host [n_rhs],
+ * dcdx_host [n_phase][nely][nelx] (may be NULL).  Host arrays may be
+ * pageable or pinned; the call synchronises. */
+mto_status mto_run_host(mto_ctx* ctx, int n_phase, const double* x_host, const double* E_phase,
+                        double penal, int n_rhs, const double* f_host, double* u_host,
+                        double* compliance_host, double* dcdx_host, mto_solve_stats* stats);
+
+/* Diagnostics for per-kernel checks.
+ * level: 0 = coarsest ... n_coarsen = finest (the numbering of Alg. 1).
+ * Vectors are device float64 in the level's own layout [ny_l+1][nx_l+1][2]
+ * with nx_l = nelx >> (n_coarsen - level).
+ * mto_apply_operator: y = K_l v with v treated as zero on clamped DOFs and y
+ * zero there; K_l is the operator the solver uses on that level in the
+ * context's precision (float32 levels compute in float32; the finest level
+ * of the mixed path offers both: use_vcycle_operator = 1 selects the
+ * bfloat16/float32 smoother operator, 0 the float64 outer operator).
+ * mto_apply_preconditioner: z = one V-cycle applied to r on the finest level
+ * (Alg. 1 from U = 0, as inside PCG). */
+mto_status mto_apply_operator(mto_ctx* ctx, int level, int use_vcycle_operator, const double* v_dev,
+                              double* y_dev);
+mto_status mto_apply_preconditioner(mto_ctx* ctx, const double* r_dev, double* z_dev);
+
+/* Mesh and hierarchy facts: number of free DOFs of the coarsest grid, number
+ * of levels, and the element moduli E (device float64 [nely][nelx]) of the
+ * last set_design. */
+mto_status mto_get_info(mto_ctx* ctx, int* n_levels, int* coarsest_free_dofs);
+mto_status mto_get_moduli(mto_ctx* ctx, double* E_dev);
+
+void mto_destroy(mto_ctx* ctx);
+const char* mto_status_string(mto_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTO_H */

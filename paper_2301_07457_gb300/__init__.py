@@ -1,0 +1,228 @@
+"""GB300 pCGMG solver for multi-material compliance topology optimisation.
+
+Python layer over libmto (C ABI in include/mto.h).  PyTorch provides device
+memory and the current CUDA stream; every arithmetic step of the solve runs in
+libmto's sm_103a kernels.  Paper: Luu & Banh, arXiv 2301.07457 -- Alg. 2
+(PCG) preconditioned by Alg. 1 (V-cycle), Eq. 5 (multi-material SIMP),
+Eqs. 6-9 (Q4 plane-stress compliance problem).
+"""
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    COARSE_GALERKIN,
+    COARSE_REDISCRETIZE,
+    EDGE_BOTTOM,
+    EDGE_LEFT,
+    EDGE_RIGHT,
+    EDGE_TOP,
+    PRECISION_FP64,
+    PRECISION_MIXED,
+    MtoError,
+    SolverOpts,
+    SolveStats,
+)
+
+__all__ = ["Mesh", "Compliance", "compliance", "MtoError", "SolverOpts", "SolveStats"]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_f64(t, device, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device != device or t.dtype != torch.float64:
+        raise ValueError(f"{name} must be a float64 tensor on {device}")
+    return t.contiguous()
+
+
+class Mesh:
+    """A square-wall mesh (nelx x nely unit Q4 elements) with its level hierarchy.
+
+    precision: "fp64" or "mixed" (float32 V-cycle with bfloat16 moduli inside a
+    float64 CG).  Other keywords are the fields of mto_solver_opts.
+    """
+
+    def __init__(self, nelx, nely, nu=0.3, fixed_edges=EDGE_BOTTOM, n_coarsen=3,
+                 precision="fp64", tol=1e-8, max_it=500, omega=0.6, nu1=2, nu2=2,
+                 coarse_kind="galerkin", rr_every=25, flexible=None, check_every=4,
+                 device=None):
+        lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        o = _lib.default_opts()
+        o.tol, o.max_it, o.omega, o.nu1, o.nu2 = tol, max_it, omega, nu1, nu2
+        o.n_coarsen = n_coarsen
+        o.coarse_kind = {"galerkin": COARSE_GALERKIN, "rediscretize": COARSE_REDISCRETIZE}[coarse_kind]
+        o.precision = {"fp64": PRECISION_FP64, "mixed": PRECISION_MIXED}[precision]
+        o.rr_every = rr_every
+        o.flexible = int(precision == "mixed") if flexible is None else int(flexible)
+        o.check_every = check_every
+        self.opts = o
+        self.nelx, self.nely, self.nu, self.fixed_edges = nelx, nely, nu, fixed_edges
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = lib.mto_create_mesh(ctypes.byref(self._h), nelx, nely, nu, fixed_edges,
+                                       ctypes.byref(o), self.device.index, _stream(self.device))
+        _lib.check(code, "mto_create_mesh")
+        self._lib = lib
+        self.n_phase = None
+        self.E_phase = None
+        self.penal = None
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.mto_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def node_shape(self):
+        return (self.nely + 1, self.nelx + 1, 2)
+
+    def info(self):
+        nl, n0 = ctypes.c_int(), ctypes.c_int()
+        _lib.check(self._lib.mto_get_info(self._h, ctypes.byref(nl), ctypes.byref(n0)), "mto_get_info")
+        return {"n_levels": nl.value, "coarsest_free_dofs": n0.value}
+
+    # -- solver --------------------------------------------------------------
+    def set_design(self, x, E_phase, penal=3.0):
+        """x: float64 [n_phase][nely][nelx] on the mesh's device (Eq. 5)."""
+        x = _dev_f64(x, self.device, "x")
+        if x.dim() != 3 or x.shape[1:] != (self.nely, self.nelx):
+            raise ValueError("x must be [n_phase][nely][nelx]")
+        E = (ctypes.c_double * len(E_phase))(*[float(e) for e in E_phase])
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_set_design(self._h, x.shape[0], _ptr(x), E, float(penal))
+        _lib.check(code, "mto_set_design")
+        self.n_phase, self.E_phase, self.penal = x.shape[0], list(E_phase), float(penal)
+        self._x = x
+
+    def solve(self, f, u0=None, raise_on_failure=True):
+        """Solve K u = f (f: [n_rhs?][nely+1][nelx+1][2] float64).  Returns (u, stats)."""
+        f = _dev_f64(f, self.device, "f")
+        batched = f.dim() == 4
+        if f.shape[-3:] != self.node_shape:
+            raise ValueError(f"f must end in {self.node_shape}")
+        u = torch.zeros_like(f) if u0 is None else _dev_f64(u0, self.device, "u0").clone()
+        n_rhs = f.shape[0] if batched else 1
+        st = SolveStats()
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_solve(self._h, n_rhs, _ptr(f), _ptr(u), ctypes.byref(st))
+        if code not in (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_BREAKDOWN) or (
+                raise_on_failure and code != _lib.OK):
+            raise MtoError(code, "mto_solve")
+        d = st.as_dict()
+        d["status"] = _lib.STATUS[code]
+        return u, d
+
+    def compliance_grad(self, f, u, want_grad=True):
+        """C_k = f_k . u_k and dC/dx summed over load cases (Eq. 6, Sec. 4)."""
+        f = _dev_f64(f, self.device, "f")
+        u = _dev_f64(u, self.device, "u")
+        n_rhs = f.shape[0] if f.dim() == 4 else 1
+        C = torch.empty(n_rhs, dtype=torch.float64, device=self.device)
+        g = None
+        if want_grad:
+            g = torch.empty((self.n_phase, self.nely, self.nelx), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_compliance_grad(self._h, n_rhs, _ptr(f), _ptr(u), _ptr(C),
+                                                 _ptr(g) if g is not None else None)
+        _lib.check(code, "mto_compliance_grad")
+        return C, g
+
+    def run_host(self, x, E_phase, penal, f, want_grad=True):
+        """set_design + solve + compliance with host (numpy, float64) buffers."""
+        import numpy as np
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        n_rhs = f.shape[0] if f.ndim == 4 else 1
+        u = np.zeros_like(f)
+        C = np.zeros(n_rhs)
+        g = np.zeros(x.shape) if want_grad else None
+        E = (ctypes.c_double * len(E_phase))(*[float(e) for e in E_phase])
+        st = SolveStats()
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_run_host(
+                self._h, x.shape[0], x.ctypes.data_as(ctypes.c_void_p), E, float(penal), n_rhs,
+                f.ctypes.data_as(ctypes.c_void_p), u.ctypes.data_as(ctypes.c_void_p),
+                C.ctypes.data_as(ctypes.c_void_p),
+                g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, ctypes.byref(st))
+        _lib.check(code, "mto_run_host")
+        return u, C, g, st.as_dict()
+
+    # -- diagnostics ---------------------------------------------------------
+    def level_shape(self, level):
+        s = self.opts.n_coarsen - level
+        return ((self.nely >> s) + 1, (self.nelx >> s) + 1, 2)
+
+    def apply_operator(self, level, v, vcycle_operator=False):
+        v = _dev_f64(v, self.device, "v")
+        y = torch.empty_like(v)
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_apply_operator(self._h, level, int(vcycle_operator), _ptr(v), _ptr(y))
+        _lib.check(code, "mto_apply_operator")
+        return y
+
+    def apply_preconditioner(self, r):
+        r = _dev_f64(r, self.device, "r")
+        z = torch.empty_like(r)
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_apply_preconditioner(self._h, _ptr(r), _ptr(z))
+        _lib.check(code, "mto_apply_preconditioner")
+        return z
+
+    def moduli(self):
+        E = torch.empty((self.nely, self.nelx), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.mto_get_moduli(self._h, _ptr(E)), "mto_get_moduli")
+        return E
+
+
+class Compliance(torch.autograd.Function):
+    """C(x) = sum_k f_k . u_k(x) with K(x) u_k = f_k; backward is the adjoint sensitivity.
+
+    The compliance problem is self-adjoint (Eq. 6), so the backward needs no
+    second solve: dC/dx_{e,i} = -p x^{p-1} E_i u_e^T KE u_e with the forward u.
+    When keep_u is False the forward does not hold u; the backward re-solves
+    for it (warm-started from zero), trading time for memory.
+    """
+
+    @staticmethod
+    def forward(ctx, x, mesh, f, E_phase, penal, keep_u=True):
+        mesh.set_design(x.detach(), E_phase, penal)
+        u, _ = mesh.solve(f)
+        C, _ = mesh.compliance_grad(f, u, want_grad=False)
+        ctx.mesh, ctx.E_phase, ctx.penal, ctx.keep_u = mesh, E_phase, penal, keep_u
+        ctx.save_for_backward(x.detach(), f, u if keep_u else torch.empty(0, device=f.device))
+        return C.sum()
+
+    @staticmethod
+    def backward(ctx, gC):
+        x, f, u = ctx.saved_tensors
+        mesh = ctx.mesh
+        mesh.set_design(x, ctx.E_phase, ctx.penal)
+        if not ctx.keep_u:
+            u, _ = mesh.solve(f)
+        _, g = mesh.compliance_grad(f, u, want_grad=True)
+        return g * gC, None, None, None, None, None
+
+
+def compliance(x, mesh, f, E_phase, penal=3.0, keep_u=True):
+    """Differentiable compliance (see Compliance)."""
+    return Compliance.apply(x, mesh, f, E_phase, penal, keep_u)

@@ -1,0 +1,823 @@
+// C ABI of libmto: context and memory plan, per-design setup, the PCG driver
+// (Alg. 2) with its V-cycle preconditioner (Alg. 1), compliance and
+// sensitivities, and the diagnostic entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mto.h"
+#include "mto_launch.h"
+
+using namespace mto;
+
+namespace {
+
+struct LevelBuf {
+  Grid g{};
+  void* z[2] = {nullptr, nullptr};  // V2<T> vectors (ping-pong)
+  void* b = nullptr;                // right-hand side of this level
+  void* coef = nullptr;             // T coefficients, NCOEF * g.size()
+  void* invd2 = nullptr;            // V2<T> w / D
+  double* mom = nullptr;            // NMOM * g.size() (coarse levels)
+  double* coef64 = nullptr;         // level 0: float64 coefficients for the dense matrix
+};
+
+}  // namespace
+
+struct mto_ctx {
+  int device = 0, num_sms = 1;
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
+  int nelx = 0, nely = 0;
+  double nu = 0.3;
+  unsigned fixed = 0;
+  mto_solver_opts o{};
+  int L = 0;
+  bool mixed = false;
+  std::vector<LevelBuf> lv;
+  // finest level
+  double* E64 = nullptr;
+  __nv_bfloat16* Ebf = nullptr;
+  double* invd1 = nullptr;
+  double2 *x = nullptr, *r = nullptr, *q = nullptr, *f = nullptr, *tmp = nullptr;
+  double2* p[2] = {nullptr, nullptr};
+  float2* r32 = nullptr;
+  // coarsest grid
+  int n0 = 0, bw0 = 0;
+  int* dof_index = nullptr;
+  double *Kd = nullptr, *Kinv = nullptr;
+  int* err_flag = nullptr;
+  // reductions
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* sc_host = nullptr;  // pinned
+  int* err_host = nullptr;        // pinned
+  // design
+  bool has_design = false;
+  int n_phase = 0;
+  PhaseTable ph{};
+  double penal = 3.0;
+  int ipenal = 3;
+  double* xdes = nullptr;
+  size_t xdes_cap = 0;
+  // host-call staging (mto_run_host)
+  double *hx = nullptr, *hf = nullptr, *hu = nullptr, *hc = nullptr, *hg = nullptr;
+  size_t hx_cap = 0, hf_cap = 0, hg_cap = 0;
+  int hc_cap = 0;
+  // graph of two PCG iterations
+  cudaGraphExec_t gexec = nullptr;
+  // constants
+  FineConst<double> kf64{};
+  FineConst<float> kf32{};
+  double w_over_kdiag = 0.0;
+  // stats
+  float ms_setup = 0.f;
+  mto_solve_stats last{};
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return MTO_ERR_CUDA;    \
+  } while (0)
+
+#define ST(call)                          \
+  do {                                    \
+    mto_status s_ = (call);               \
+    if (s_ != MTO_OK) return s_;          \
+  } while (0)
+
+mto_status dalloc(mto_ctx* c, void** out, size_t bytes) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(out, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MTO_ERR_OOM;
+  }
+  c->allocs.push_back(*out);
+  if (cudaMemset(*out, 0, bytes) != cudaSuccess) return MTO_ERR_CUDA;
+  return MTO_OK;
+}
+
+template <typename P> mto_status dalloc_t(mto_ctx* c, P** out, size_t count) {
+  void* v = nullptr;
+  mto_status s = dalloc(c, &v, count * sizeof(P));
+  *out = static_cast<P*>(v);
+  return s;
+}
+
+// Make the context's stream wait for the caller's stream, and back.
+mto_status enter(mto_ctx* c) {
+  CK(cudaSetDevice(c->device));
+  CK(cudaEventRecord(c->ev_in, c->user_stream));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  return MTO_OK;
+}
+mto_status leave(mto_ctx* c) {
+  CK(cudaEventRecord(c->ev_out, c->stream));
+  CK(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+  return MTO_OK;
+}
+
+int target_warps(const mto_ctx* c) { return c->num_sms * 32; }
+
+// ---------------------------------------------------------------------------
+// Sweep helpers
+// ---------------------------------------------------------------------------
+template <typename T> SweepParams<T> base_params(const mto_ctx* c, const Grid& g) {
+  SweepParams<T> p;
+  std::memset(&p, 0, sizeof(p));
+  p.g = g;
+  p.cstride = g.size();
+  p.partials = c->partials;
+  p.ticket = c->ticket;
+  return p;
+}
+
+template <typename T> FineConst<T> fine_const(const mto_ctx* c);
+template <> FineConst<double> fine_const<double>(const mto_ctx* c) { return c->kf64; }
+template <> FineConst<float> fine_const<float>(const mto_ctx* c) { return c->kf32; }
+
+// One V-cycle (Alg. 1) on coarse level l >= 1 with right-hand side lv[l].b.
+// Returns the index of the z buffer that holds the result.
+template <typename T>
+mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
+  using T2 = typename V2<T>::t;
+  LevelBuf& L = c->lv[l];
+  LevelBuf& C = c->lv[l - 1];
+  const int tw = target_warps(c);
+  const int nb = vec_blocks(L.g.size(), c->num_sms);
+  // First pre-smoothing sweep from U = 0: U = w D^-1 F.
+  CK(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb, c->stream));
+  int cur = 0;
+  auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc) -> cudaError_t {
+    SweepParams<T> p = base_params<T>(c, L.g);
+    p.gc = C.g;
+    p.gate = 1;
+    p.sc = sc;
+    p.v = v;
+    p.zc = zc;
+    p.b = (const T2*)L.b;
+    p.out = out;
+    p.bc = (T2*)C.b;
+    p.coef = (const T*)L.coef;
+    p.invd2 = (const T2*)L.invd2;
+    return launch_sweep<T>(SRC_COARSE, mode, false, false, p, sweep_shape(L.g, mode, tw), c->stream);
+  };
+  for (int s = 1; s < c->o.nu1; ++s) {
+    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
+    cur ^= 1;
+  }
+  CK(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
+  int cidx = 0;
+  if (l - 1 == 0) {
+    CK(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
+                               (T2*)C.z[0], sc, c->stream));
+  } else {
+    ST(coarse_cycle<T>(c, l - 1, sc, &cidx));
+  }
+  CK(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));
+  cur ^= 1;
+  for (int s = 1; s < c->o.nu2; ++s) {
+    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
+    cur ^= 1;
+  }
+  *final_idx = cur;
+  return MTO_OK;
+}
+
+// V-cycle on the finest level with right-hand side r (float64).  With
+// with_dot, the last post-smoothing sweep also forms z.r (and z.q) and
+// finishes beta (FIN_RHO).
+template <typename T>
+mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx) {
+  using T2 = typename V2<T>::t;
+  constexpr bool MIX = sizeof(T) == 4;
+  LevelBuf& L = c->lv[c->L];
+  LevelBuf& C = c->lv[c->L - 1];
+  const int tw = target_warps(c);
+  const int nb = vec_blocks(L.g.size(), c->num_sms);
+  const int src = MIX ? SRC_FINEBF : SRC_FINE64;
+  const T2* b;
+  if constexpr (MIX) {
+    CK(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r, c->r32, (float2*)L.z[0], sc,
+                             nb, c->stream));
+    b = (const T2*)c->r32;
+  } else {
+    CK(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->stream));
+    b = (const T2*)c->r;
+  }
+  int cur = 0;
+  auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc, bool dot) -> cudaError_t {
+    SweepParams<T> p = base_params<T>(c, L.g);
+    p.gc = C.g;
+    p.gate = 1;
+    p.sc = sc;
+    p.v = v;
+    p.zc = zc;
+    p.b = b;
+    p.out = out;
+    p.bc = (T2*)C.b;
+    p.E = MIX ? (const void*)c->Ebf : (const void*)c->E64;
+    p.kf = fine_const<T>(c);
+    p.invd1 = c->invd1;
+    p.wdiag = T(c->w_over_kdiag);
+    if (dot) {
+      p.rdot = c->r;
+      p.qdot = c->o.flexible ? c->q : nullptr;
+      p.finish = FIN_RHO;
+    }
+    return launch_sweep<T>(src, mode, dot, false, p, sweep_shape(L.g, mode, tw), c->stream);
+  };
+  for (int s = 1; s < c->o.nu1; ++s) {
+    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr, false));
+    cur ^= 1;
+  }
+  CK(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr, false));
+  int cidx = 0;
+  if (c->L - 1 == 0) {
+    CK(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
+                               (T2*)C.z[0], sc, c->stream));
+  } else {
+    ST(coarse_cycle<T>(c, c->L - 1, sc, &cidx));
+  }
+  CK(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx],
+           with_dot && c->o.nu2 == 1));
+  cur ^= 1;
+  for (int s = 1; s < c->o.nu2; ++s) {
+    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr,
+             with_dot && s == c->o.nu2 - 1));
+    cur ^= 1;
+  }
+  *final_idx = cur;
+  return MTO_OK;
+}
+
+// out = b - K v on the finest level in float64 (RESID), with a finishing action.
+mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* out, int finish,
+                      int gate, int replace_gate) {
+  const Grid& g = c->lv[c->L].g;
+  SweepParams<double> p = base_params<double>(c, g);
+  p.gate = gate;
+  p.replace_gate = replace_gate;
+  p.sc = c->sc;
+  p.v = v;
+  p.b = b;
+  p.out = out;
+  p.E = c->E64;
+  p.kf = c->kf64;
+  p.finish = finish;
+  CK(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
+                          sweep_shape(g, MODE_RESID, target_warps(c)), c->stream));
+  return MTO_OK;
+}
+
+// One PCG iteration (Alg. 2) with search directions p[par] -> p[par ^ 1].
+mto_status enqueue_iteration(mto_ctx* c, int par) {
+  const Grid& g = c->lv[c->L].g;
+  int zi = 0;
+  const void* z;
+  if (c->mixed) {
+    ST(fine_cycle<float>(c, c->sc, true, &zi));
+  } else {
+    ST(fine_cycle<double>(c, c->sc, true, &zi));
+  }
+  z = c->lv[c->L].z[zi];
+  {
+    SweepParams<double> p = base_params<double>(c, g);
+    p.gate = 1;
+    p.sc = c->sc;
+    p.v = c->p[par];
+    p.zkp = z;
+    p.p_out = c->p[par ^ 1];
+    p.out = c->q;
+    p.E = c->E64;
+    p.kf = c->kf64;
+    p.finish = FIN_PQ;
+    CK(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
+                            sweep_shape(g, MODE_KP, target_warps(c)), c->stream));
+  }
+  CK(launch_update(g, c->x, c->r, c->p[par ^ 1], c->q, c->partials, c->ticket, c->sc,
+                   vec_blocks(g.size(), c->num_sms), c->stream));
+  if (c->mixed && c->o.rr_every > 0) ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1));
+  return MTO_OK;
+}
+
+mto_status build_graph(mto_ctx* c) {
+  if (c->gexec) return MTO_OK;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  mto_status s0 = enqueue_iteration(c, 0);
+  mto_status s1 = s0 == MTO_OK ? enqueue_iteration(c, 1) : s0;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (s1 != MTO_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return s1;
+  }
+  if (e != cudaSuccess) return MTO_ERR_CUDA;
+  e = cudaGraphInstantiate(&c->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->gexec = nullptr;
+    return MTO_ERR_CUDA;
+  }
+  return MTO_OK;
+}
+
+bool valid_opts(const mto_solver_opts& o) {
+  return o.tol >= 0.0 && o.max_it >= 0 && o.omega > 0.0 && o.omega <= 1.0 && o.nu1 >= 1 &&
+         o.nu2 >= 1 && o.nu1 <= 16 && o.nu2 <= 16 && o.n_coarsen >= 1 && o.n_coarsen <= 14 &&
+         (o.coarse_kind == MTO_COARSE_GALERKIN || o.coarse_kind == MTO_COARSE_REDISCRETIZE) &&
+         (o.precision == MTO_PRECISION_FP64 || o.precision == MTO_PRECISION_MIXED) &&
+         o.rr_every >= 0 && o.check_every >= 1;
+}
+
+mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_out) {
+  const Grid& g = c->lv[c->L].g;
+  CK(launch_pack(g, f_dev, c->f, c->stream, c->num_sms));
+  CK(launch_pack(g, u_dev, c->x, c->stream, c->num_sms));
+  DevScalars s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.tol2 = c->o.tol * c->o.tol;
+  s0.max_it = c->o.max_it;
+  s0.flexible = c->o.flexible;
+  s0.rr_every = c->mixed ? c->o.rr_every : 0;
+  *c->sc_host = s0;
+  CK(cudaMemcpyAsync(c->sc, c->sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->p[0], 0, sizeof(double2) * g.size(), c->stream));
+  CK(launch_dot(g.size(), c->f, c->f, c->partials, c->ticket, c->sc, FIN_FF, nullptr,
+                vec_blocks(g.size(), c->num_sms), c->stream));
+  ST(fine_resid(c, c->x, c->f, c->r, FIN_INIT_RR, 0, 0));
+  ST(build_graph(c));
+  const int poll = (c->o.check_every + 1) / 2;  // graph launches (2 iterations each) per poll
+  int launched = 0;
+  for (;;) {
+    CK(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->sc_host->done != RUNNING || launched > c->o.max_it + 2) break;
+    for (int k = 0; k < poll; ++k) {
+      CK(cudaGraphLaunch(c->gexec, c->stream));
+      launched += 2;
+    }
+  }
+  ST(fine_resid(c, c->x, c->f, c->tmp, FIN_TRUE, 0, 0));
+  CK(launch_unpack(g, c->x, u_dev, c->stream, c->num_sms));
+  CK(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const DevScalars& h = *c->sc_host;
+  const double fn = std::sqrt(h.ff);
+  c->last.iters = h.iter;
+  c->last.converged = h.done == CONVERGED;
+  c->last.rel_res_rec = fn > 0 ? std::sqrt(h.rr) / fn : 0.0;
+  c->last.rel_res_true = fn > 0 ? std::sqrt(h.rr_true) / fn : 0.0;
+  *iters_out = h.iter;
+  if (h.done == BREAKDOWN) return MTO_ERR_BREAKDOWN;
+  if (h.done != CONVERGED) return MTO_ERR_NOT_CONVERGED;
+  return MTO_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public API
+// ===========================================================================
+
+extern "C" {
+
+void mto_default_opts(mto_solver_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->max_it = 500;
+  o->omega = 0.6;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->n_coarsen = 3;
+  o->coarse_kind = MTO_COARSE_GALERKIN;
+  o->precision = MTO_PRECISION_FP64;
+  o->rr_every = 25;
+  o->flexible = 0;
+  o->check_every = 4;
+}
+
+const char* mto_status_string(mto_status s) {
+  switch (s) {
+    case MTO_OK: return "ok";
+    case MTO_ERR_ARG: return "invalid argument";
+    case MTO_ERR_UNSUPPORTED_MESH: return "unsupported mesh";
+    case MTO_ERR_OOM: return "out of device memory";
+    case MTO_ERR_CUDA: return "CUDA error";
+    case MTO_ERR_NOT_CONVERGED: return "not converged";
+    case MTO_ERR_BREAKDOWN: return "PCG breakdown";
+    case MTO_ERR_TIMEOUT: return "device wait timed out";
+    case MTO_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+void mto_destroy(mto_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->sc_host) cudaFreeHost(c->sc_host);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigned fixed,
+                              const mto_solver_opts& o, int device, void* stream) {
+  c->device = device;
+  c->nelx = nelx;
+  c->nely = nely;
+  c->nu = nu;
+  c->fixed = fixed;
+  c->o = o;
+  c->L = o.n_coarsen;
+  c->mixed = o.precision == MTO_PRECISION_MIXED;
+  c->user_stream = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(device));
+  CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  CK(cudaEventCreate(&c->ev_a));
+  CK(cudaEventCreate(&c->ev_b));
+  CK(cudaMallocHost(&c->sc_host, sizeof(DevScalars)));
+  CK(cudaMallocHost(&c->err_host, sizeof(int)));
+
+  // Element-operator constants (plane stress, Eq. 8; strain basis, mto_common.cuh).
+  const double kap = 1.0 / (4.0 * (1.0 - nu * nu)), gs = 0.5 * (1.0 - nu);
+  c->kf64 = {kap, kap * nu, kap * (1.0 + gs) / 3.0, kap * gs};
+  c->kf32 = {(float)c->kf64.kA, (float)c->kf64.kB, (float)c->kf64.kC, (float)c->kf64.kG};
+  const double kdiag = kap * (1.0 + (1.0 + gs) / 3.0 + gs);  // KE_00 at E = 1
+  c->w_over_kdiag = o.omega / kdiag;
+
+  c->lv.resize(c->L + 1);
+  for (int l = 0; l <= c->L; ++l) {
+    const int sh = c->L - l;
+    c->lv[l].g = make_grid(nelx >> sh, nely >> sh, fixed);
+  }
+  const size_t vsz = c->mixed ? sizeof(float2) : sizeof(double2);
+  const size_t csz = c->mixed ? sizeof(float) : sizeof(double);
+  for (int l = 0; l <= c->L; ++l) {
+    LevelBuf& B = c->lv[l];
+    const size_t n = (size_t)B.g.size();
+    ST(dalloc(c, &B.z[0], n * vsz));
+    ST(dalloc(c, &B.z[1], n * vsz));
+    if (l < c->L) {
+      ST(dalloc(c, &B.b, n * vsz));
+      ST(dalloc(c, &B.coef, n * NCOEF * csz));
+      ST(dalloc(c, &B.invd2, n * vsz));
+      ST(dalloc_t(c, &B.mom, n * NMOM));
+    }
+    if (l == 0) ST(dalloc_t(c, &B.coef64, n * NCOEF));
+  }
+  const Grid& gf = c->lv[c->L].g;
+  const size_t nf = (size_t)gf.size();
+  ST(dalloc_t(c, &c->E64, nf));
+  if (c->mixed) {
+    ST(dalloc_t(c, &c->Ebf, nf));
+    ST(dalloc_t(c, &c->r32, nf));
+  } else {
+    ST(dalloc_t(c, &c->invd1, nf));
+  }
+  ST(dalloc_t(c, &c->x, nf));
+  ST(dalloc_t(c, &c->r, nf));
+  ST(dalloc_t(c, &c->q, nf));
+  ST(dalloc_t(c, &c->f, nf));
+  ST(dalloc_t(c, &c->tmp, nf));
+  ST(dalloc_t(c, &c->p[0], nf));
+  ST(dalloc_t(c, &c->p[1], nf));
+
+  // Coarsest grid: free-DOF numbering (row-major over nodes, u_x before u_y),
+  // its inverse map, and the half bandwidth of K_0 in that numbering.
+  const Grid& g0 = c->lv[0].g;
+  std::vector<int> idx(2 * (size_t)g0.size() + 1, -1);
+  std::vector<int> inv;
+  for (int j = 0; j <= g0.ny; ++j)
+    for (int i = 0; i <= g0.nx; ++i)
+      if (!g0.is_fixed(i, j))
+        for (int comp = 0; comp < 2; ++comp) {
+          idx[2 * g0.at(i, j) + comp] = (int)inv.size();
+          inv.push_back((int)(2 * g0.at(i, j) + comp));
+        }
+  c->n0 = (int)inv.size();
+  if (c->n0 > 4096) return MTO_ERR_UNSUPPORTED_MESH;
+  int bw = 0;
+  for (int j = 0; j <= g0.ny; ++j)
+    for (int i = 0; i <= g0.nx; ++i)
+      for (int comp = 0; comp < 2; ++comp) {
+        const int a = idx[2 * g0.at(i, j) + comp];
+        if (a < 0) continue;
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            if (!g0.valid(i + di, j + dj)) continue;
+            for (int c2 = 0; c2 < 2; ++c2) {
+              const int b = idx[2 * g0.at(i + di, j + dj) + c2];
+              if (b >= 0 && std::abs(a - b) > bw) bw = std::abs(a - b);
+            }
+          }
+      }
+  c->bw0 = bw;
+  std::vector<int> dof(2 * (size_t)g0.size() + c->n0);
+  std::memcpy(dof.data(), idx.data(), sizeof(int) * 2 * (size_t)g0.size());
+  std::memcpy(dof.data() + 2 * (size_t)g0.size(), inv.data(), sizeof(int) * c->n0);
+  ST(dalloc_t(c, &c->dof_index, dof.size()));
+  CK(cudaMemcpy(c->dof_index, dof.data(), sizeof(int) * dof.size(), cudaMemcpyHostToDevice));
+  ST(dalloc_t(c, &c->Kd, (size_t)c->n0 * c->n0));
+  ST(dalloc_t(c, &c->Kinv, (size_t)c->n0 * c->n0));
+  ST(dalloc_t(c, &c->err_flag, 1));
+
+  // Reduction scratch: two partials per block of the largest launch.
+  int maxb = vec_blocks(gf.size(), c->num_sms);
+  for (int mode = 0; mode <= MODE_RESTRICT; ++mode) {
+    const SweepShape s = sweep_shape(gf, mode, target_warps(c));
+    if (s.nblocks > maxb) maxb = s.nblocks;
+  }
+  ST(dalloc_t(c, &c->partials, 2 * (size_t)maxb + 2));
+  ST(dalloc_t(c, &c->ticket, 4));
+  ST(dalloc_t(c, &c->sc, 1));
+  return MTO_OK;
+}
+
+mto_status mto_create_mesh(mto_ctx** out, int nelx, int nely, double nu, unsigned fixed_edges,
+                           const mto_solver_opts* opts, int device, void* cuda_stream) {
+  if (!out) return MTO_ERR_ARG;
+  *out = nullptr;
+  mto_solver_opts o;
+  mto_default_opts(&o);
+  if (opts) o = *opts;
+  if (nelx < 1 || nely < 1 || !(nu > -1.0 && nu < 0.5) || fixed_edges == 0u || fixed_edges > 15u ||
+      !valid_opts(o) || device < 0)
+    return MTO_ERR_ARG;
+  if (nelx % (1 << o.n_coarsen) || nely % (1 << o.n_coarsen)) return MTO_ERR_UNSUPPORTED_MESH;
+  if ((long long)nelx * nely > (1LL << 30)) return MTO_ERR_UNSUPPORTED_MESH;
+  mto_ctx* c = new (std::nothrow) mto_ctx();
+  if (!c) return MTO_ERR_OOM;
+  mto_status s = create_impl(c, nelx, nely, nu, fixed_edges, o, device, cuda_stream);
+  if (s != MTO_OK) {
+    cudaGetLastError();
+    mto_destroy(c);
+    return s;
+  }
+  *out = c;
+  return MTO_OK;
+}
+
+static mto_status set_design_impl(mto_ctx* c, int n_phase, const double* x_dev,
+                                  const double* E_phase, double penal) {
+  const Grid& gf = c->lv[c->L].g;
+  const size_t nel = (size_t)c->nelx * c->nely;
+  if (c->xdes_cap < (size_t)n_phase * nel) {
+    ST(dalloc_t(c, &c->xdes, (size_t)n_phase * nel));
+    c->xdes_cap = (size_t)n_phase * nel;
+  }
+  c->n_phase = n_phase;
+  for (int i = 0; i < 16; ++i) c->ph.E[i] = i < n_phase ? E_phase[i] : 0.0;
+  c->penal = penal;
+  c->ipenal = (penal == std::floor(penal) && penal <= 16.0) ? (int)penal : -1;
+  CK(cudaEventRecord(c->ev_a, c->stream));
+  CK(cudaMemcpyAsync(c->xdes, x_dev, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  CK(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->stream,
+                    c->num_sms));
+  if (!c->mixed) CK(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->stream, c->num_sms));
+  const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
+  for (int l = c->L - 1; l >= 0; --l) {
+    LevelBuf& B = c->lv[l];
+    if (l == c->L - 1) {
+      CK(launch_moments_from_fine(B.g, gf, c->mixed ? nullptr : c->E64, c->mixed ? c->Ebf : nullptr,
+                                  redisc, B.mom, c->stream, c->num_sms));
+    } else {
+      CK(launch_moments_from_coarse(B.g, c->lv[l + 1].g, c->lv[l + 1].mom, redisc, B.mom, c->stream,
+                                    c->num_sms));
+    }
+    if (c->mixed) {
+      CK(launch_coefs<float>(B.g, B.mom, c->nu, (float*)B.coef, c->stream, c->num_sms));
+      if (l > 0)
+        CK(launch_coarse_invd<float>(B.g, (const float*)B.coef, c->o.omega, (float2*)B.invd2,
+                                     c->stream, c->num_sms));
+    } else {
+      CK(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->stream, c->num_sms));
+      if (l > 0)
+        CK(launch_coarse_invd<double>(B.g, (const double*)B.coef, c->o.omega, (double2*)B.invd2,
+                                      c->stream, c->num_sms));
+    }
+  }
+  LevelBuf& B0 = c->lv[0];
+  CK(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->stream, c->num_sms));
+  CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * c->n0, c->stream));
+  CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
+  CK(launch_dense_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->Kd, c->stream));
+  CK(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->Kinv, c->err_flag, c->stream, c->num_sms));
+  CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaEventRecord(c->ev_b, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaEventElapsedTime(&c->ms_setup, c->ev_a, c->ev_b));
+  if (*c->err_host) return MTO_ERR_BREAKDOWN;
+  c->has_design = true;
+  return MTO_OK;
+}
+
+mto_status mto_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
+                          double penal) {
+  if (!c || !x_dev || !E_phase || n_phase < 1 || n_phase > 16 || !(penal >= 1.0 && penal <= 64.0))
+    return MTO_ERR_ARG;
+  for (int i = 0; i < n_phase; ++i)
+    if (!(E_phase[i] > 0.0 && E_phase[i] < 1e300)) return MTO_ERR_ARG;
+  ST(enter(c));
+  c->has_design = false;
+  mto_status s = set_design_impl(c, n_phase, x_dev, E_phase, penal);
+  mto_status s2 = leave(c);
+  return s != MTO_OK ? s : s2;
+}
+
+mto_status mto_solve(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev,
+                     mto_solve_stats* stats) {
+  if (!c || n_rhs < 1 || !f_dev || !u_dev) return MTO_ERR_ARG;
+  if (!c->has_design) return MTO_ERR_STATE;
+  ST(enter(c));
+  const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
+  mto_status worst = MTO_OK;
+  int total_it = 0;
+  CK(cudaEventRecord(c->ev_a, c->stream));
+  for (int k = 0; k < n_rhs; ++k) {
+    int it = 0;
+    mto_status s = solve_one(c, f_dev + k * nd, u_dev + k * nd, &it);
+    total_it += it;
+    if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM) {
+      leave(c);
+      return s;
+    }
+    if (s != MTO_OK && worst == MTO_OK) worst = s;
+  }
+  CK(cudaEventRecord(c->ev_b, c->stream));
+  CK(cudaEventSynchronize(c->ev_b));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+  c->last.iters = total_it;
+  c->last.ms_solve = ms;
+  c->last.ms_setup = c->ms_setup;
+  ST(leave(c));
+  if (stats) *stats = c->last;
+  return worst;
+}
+
+mto_status mto_last_stats(mto_ctx* c, mto_solve_stats* stats) {
+  if (!c || !stats) return MTO_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  *stats = c->last;
+  return MTO_OK;
+}
+
+mto_status mto_compliance_grad(mto_ctx* c, int n_rhs, const double* f_dev, const double* u_dev,
+                               double* compliance_dev, double* dcdx_dev) {
+  if (!c || n_rhs < 1 || !f_dev || !u_dev || !compliance_dev) return MTO_ERR_ARG;
+  if (!c->has_design) return MTO_ERR_STATE;
+  ST(enter(c));
+  const long long nn = (long long)(c->nelx + 1) * (c->nely + 1);
+  for (int k = 0; k < n_rhs; ++k) {
+    const double2* fk = reinterpret_cast<const double2*>(f_dev + 2 * nn * k);
+    const double2* uk = reinterpret_cast<const double2*>(u_dev + 2 * nn * k);
+    CK(launch_dot(nn, fk, uk, c->partials, c->ticket, nullptr, FIN_NONE, compliance_dev + k,
+                  vec_blocks(nn, c->num_sms), c->stream));
+    if (dcdx_dev)
+      CK(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
+                            c->kf64, u_dev + 2 * nn * k, dcdx_dev, k > 0, c->stream, c->num_sms));
+  }
+  return leave(c);
+}
+
+static mto_status grow(mto_ctx* c, double** p, size_t* cap, size_t need) {
+  if (*cap >= need) return MTO_OK;
+  ST(dalloc_t(c, p, need));
+  *cap = need;
+  return MTO_OK;
+}
+
+mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const double* E_phase,
+                        double penal, int n_rhs, const double* f_host, double* u_host,
+                        double* compliance_host, double* dcdx_host, mto_solve_stats* stats) {
+  if (!c || !x_host || !E_phase || n_rhs < 1 || !f_host || !u_host || !compliance_host ||
+      n_phase < 1 || n_phase > 16)
+    return MTO_ERR_ARG;
+  const size_t nel = (size_t)c->nelx * c->nely;
+  const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
+  ST(grow(c, &c->hx, &c->hx_cap, (size_t)n_phase * nel));
+  size_t fcap = c->hf_cap;
+  ST(grow(c, &c->hf, &c->hf_cap, (size_t)n_rhs * nd));
+  ST(grow(c, &c->hu, &fcap, (size_t)n_rhs * nd));
+  size_t ccap = (size_t)c->hc_cap;
+  ST(grow(c, &c->hc, &ccap, (size_t)n_rhs));
+  c->hc_cap = (int)ccap;
+  if (dcdx_host) ST(grow(c, &c->hg, &c->hg_cap, (size_t)n_phase * nel));
+  ST(enter(c));
+  CK(cudaMemcpyAsync(c->hx, x_host, sizeof(double) * n_phase * nel, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->hf, f_host, sizeof(double) * n_rhs * nd, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->hu, 0, sizeof(double) * n_rhs * nd, c->stream));
+  c->has_design = false;
+  ST(set_design_impl(c, n_phase, c->hx, E_phase, penal));
+  // The context's stream is already ordered after the caller's; solve and
+  // compliance re-enter harmlessly.
+  mto_status s = mto_solve(c, n_rhs, c->hf, c->hu, stats);
+  if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM) return s;
+  ST(mto_compliance_grad(c, n_rhs, c->hf, c->hu, c->hc, dcdx_host ? c->hg : nullptr));
+  CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * n_rhs * nd, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(compliance_host, c->hc, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, c->stream));
+  if (dcdx_host)
+    CK(cudaMemcpyAsync(dcdx_host, c->hg, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ST(leave(c));
+  return s;
+}
+
+mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, const double* v_dev,
+                              double* y_dev) {
+  if (!c || !v_dev || !y_dev || level < 0 || level > c->L) return MTO_ERR_ARG;
+  if (!c->has_design) return MTO_ERR_STATE;
+  ST(enter(c));
+  LevelBuf& B = c->lv[level];
+  const int tw = target_warps(c);
+  const bool fine = level == c->L;
+  if (fine && (!c->mixed || !use_vcycle_operator)) {
+    CK(launch_pack(B.g, v_dev, c->tmp, c->stream, c->num_sms));
+    SweepParams<double> p = base_params<double>(c, B.g);
+    p.v = c->tmp;
+    p.out = c->q;
+    p.E = c->E64;
+    p.kf = c->kf64;
+    CK(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
+                            sweep_shape(B.g, MODE_APPLY, tw), c->stream));
+    CK(launch_unpack(B.g, c->q, y_dev, c->stream, c->num_sms));
+  } else if (c->mixed) {
+    CK(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->stream, c->num_sms));
+    SweepParams<float> p = base_params<float>(c, B.g);
+    p.v = (const float2*)B.z[0];
+    p.out = (float2*)B.z[1];
+    p.E = c->Ebf;
+    p.kf = c->kf32;
+    p.coef = (const float*)B.coef;
+    CK(launch_sweep<float>(fine ? SRC_FINEBF : SRC_COARSE, MODE_APPLY, false, false, p,
+                           sweep_shape(B.g, MODE_APPLY, tw), c->stream));
+    CK(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->stream, c->num_sms));
+  } else {
+    CK(launch_pack(B.g, v_dev, (double2*)B.z[0], c->stream, c->num_sms));
+    SweepParams<double> p = base_params<double>(c, B.g);
+    p.v = (const double2*)B.z[0];
+    p.out = (double2*)B.z[1];
+    p.coef = (const double*)B.coef;
+    CK(launch_sweep<double>(SRC_COARSE, MODE_APPLY, false, false, p,
+                            sweep_shape(B.g, MODE_APPLY, tw), c->stream));
+    CK(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->stream, c->num_sms));
+  }
+  return leave(c);
+}
+
+mto_status mto_apply_preconditioner(mto_ctx* c, const double* r_dev, double* z_dev) {
+  if (!c || !r_dev || !z_dev) return MTO_ERR_ARG;
+  if (!c->has_design) return MTO_ERR_STATE;
+  ST(enter(c));
+  LevelBuf& B = c->lv[c->L];
+  CK(launch_pack(B.g, r_dev, c->r, c->stream, c->num_sms));
+  int zi = 0;
+  if (c->mixed) {
+    ST(fine_cycle<float>(c, nullptr, false, &zi));
+    CK(launch_unpack_f32(B.g, (const float2*)B.z[zi], z_dev, c->stream, c->num_sms));
+  } else {
+    ST(fine_cycle<double>(c, nullptr, false, &zi));
+    CK(launch_unpack(B.g, (const double2*)B.z[zi], z_dev, c->stream, c->num_sms));
+  }
+  return leave(c);
+}
+
+mto_status mto_get_info(mto_ctx* c, int* n_levels, int* coarsest_free_dofs) {
+  if (!c) return MTO_ERR_ARG;
+  if (n_levels) *n_levels = c->L + 1;
+  if (coarsest_free_dofs) *coarsest_free_dofs = c->n0;
+  return MTO_OK;
+}
+
+mto_status mto_get_moduli(mto_ctx* c, double* E_dev) {
+  if (!c || !E_dev) return MTO_ERR_ARG;
+  if (!c->has_design) return MTO_ERR_STATE;
+  ST(enter(c));
+  CK(launch_unpack_elems(c->lv[c->L].g, c->E64, E_dev, c->stream, c->num_sms));
+  return leave(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Host-side launchers of libmto's kernels (one translation unit each for the
+// float64 sweeps, the float32 sweeps, the setup and the vector kernels).
+#pragma once
+
+#include "mto_sweep.cuh"
+
+namespace mto {
+
+// Launch shape of a sweep over grid g (see mto_sweep.cuh).  target_warps is
+// the number of warps the launch should expose (a multiple of the SM count).
+struct SweepShape {
+  int nstrips, nchunks, H, nblocks;
+};
+SweepShape sweep_shape(const Grid& g, int mode, int target_warps);
+
+template <typename T>
+cudaError_t launch_sweep(int src, int mode, bool dot, bool zfloat, SweepParams<T> p,
+                         const SweepShape& sh, cudaStream_t s);
+
+// ---- pointwise kernels (mto_vec.cu) ----
+constexpr int VEC_NT = 256;
+int vec_blocks(long long n, int num_sms);
+
+// z = invd1 (.) r on the float64 finest level.
+cudaError_t launch_jacobi0_fine64(const Grid& g, const double* invd1, const double2* r, double2* z,
+                                  DevScalars* sc, int nblocks, cudaStream_t s);
+// r32 = float(r); z = w / (KE_00 sum E) (.) r32 on the float32 finest level.
+cudaError_t launch_jacobi0_finebf(const Grid& g, const __nv_bfloat16* E, float wdiag,
+                                  const double2* r, float2* r32, float2* z, DevScalars* sc,
+                                  int nblocks, cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi0_coarse(const Grid& g, const typename V2<T>::t* invd2,
+                                  const typename V2<T>::t* b, typename V2<T>::t* z,
+                                  DevScalars* sc, int nblocks, cudaStream_t s);
+// x += alpha p; r -= alpha q; rr = |r|^2 (FIN_UPDATE).
+cudaError_t launch_update(const Grid& g, double2* x, double2* r, const double2* p, const double2* q,
+                          double* partials, unsigned* ticket, DevScalars* sc, int nblocks,
+                          cudaStream_t s);
+// sum a.b over n double2 values (finish kind applied to sc, result also to out_value).
+cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* partials,
+                       unsigned* ticket, DevScalars* sc, int finish, double* out_value,
+                       int nblocks, cudaStream_t s);
+// dense [ny+1][nx+1][2] <-> padded layout (pack zeroes clamped DOFs).
+cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms);
+cudaError_t launch_unpack(const Grid& g, const double2* src, double* dst, cudaStream_t s, int num_sms);
+cudaError_t launch_pack_f32(const Grid& g, const double* src, float2* dst, cudaStream_t s, int num_sms);
+cudaError_t launch_unpack_f32(const Grid& g, const float2* src, double* dst, cudaStream_t s, int num_sms);
+cudaError_t launch_unpack_elems(const Grid& g, const double* src, double* dst, cudaStream_t s,
+                                int num_sms);
+// Coarsest grid: z0 = K0^-1 b0 with the dense inverse (n x n, row-major).
+template <typename T>
+cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, const double* Kinv,
+                                 const typename V2<T>::t* b, typename V2<T>::t* z,
+                                 DevScalars* sc, cudaStream_t s);
+
+// ---- setup kernels (mto_setup.cu) ----
+struct PhaseTable {
+  double E[16];
+};
+// E_e = sum_i x_{e,i}^penal E_i (Eq. 5); ipenal >= 0 selects repeated products.
+cudaError_t launch_modulus(const Grid& g, int n_phase, const double* x, PhaseTable ph, double penal,
+                           int ipenal, double* E64, __nv_bfloat16* Ebf, cudaStream_t s, int num_sms);
+// w / D on the float64 finest level (D = KE_00 * sum of the four moduli).
+cudaError_t launch_fine_invd(const Grid& g, const double* E64, double w_over_kdiag, double* invd1,
+                             cudaStream_t s, int num_sms);
+// Moments of the first coarse level from the fine moduli (float64 or bf16).
+cudaError_t launch_moments_from_fine(const Grid& gc, const Grid& gf, const double* E64,
+                                     const __nv_bfloat16* Ebf, int rediscretize, double* mom,
+                                     cudaStream_t s, int num_sms);
+// Moments of level l-1 from those of level l.
+cudaError_t launch_moments_from_coarse(const Grid& gc, const Grid& gf, const double* momf,
+                                       int rediscretize, double* momc, cudaStream_t s, int num_sms);
+template <typename T>
+cudaError_t launch_coefs(const Grid& g, const double* mom, double nu, T* coef, cudaStream_t s,
+                         int num_sms);
+template <typename T>
+cudaError_t launch_coarse_invd(const Grid& g, const T* coef, double omega,
+                               typename V2<T>::t* invd2, cudaStream_t s, int num_sms);
+// Dense coarsest matrix from float64 coefficients of level 0 (rows of free DOFs).
+cudaError_t launch_dense_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
+                                  double* Kd, cudaStream_t s);
+// In-place banded Cholesky of Kd (lower triangle), then the explicit inverse.
+cudaError_t launch_cholesky_inverse(int n, int bw, double* Kd, double* Kinv, int* err_flag,
+                                    cudaStream_t s, int num_sms);
+// dcdx (+)= -penal x^(penal-1) E_i w_e, w_e = u_e^T KE u_e (dense user layouts).
+cudaError_t launch_sensitivity(int nelx, int nely, int n_phase, const double* x, PhaseTable ph,
+                               double penal, int ipenal, FineConst<double> kf, const double* u,
+                               double* dcdx, int accumulate, cudaStream_t s, int num_sms);
+
+}  // namespace mto

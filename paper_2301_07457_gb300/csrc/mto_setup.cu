@@ -1,0 +1,420 @@
+// Per-design setup of the level hierarchy and the compliance sensitivities:
+//   * element moduli E_e = sum_i x_{e,i}^p E_i (Eq. 5), float64 and bfloat16;
+//   * the Jacobi diagonal D of the finest level (Sec. 2.3);
+//   * coarse operators: Galerkin moments of the fine moduli per coarse
+//     element (exact P^T K P for nested bilinear spaces) or the rediscretised
+//     mean modulus (Sec. 2.1), their 13 strain-basis coefficients and the
+//     Jacobi diagonals of every coarse level;
+//   * the coarsest grid (Alg. 1, l = 0): dense K_0 on the free DOFs, its
+//     Cholesky factor (Alg. 3) restricted to the band, and K_0^-1;
+//   * sensitivities dC/dx_{e,i} = -p x^{p-1} E_i u_e^T KE u_e (Eq. 6, Sec. 4).
+#include "mto_launch.h"
+
+namespace mto {
+
+__device__ __forceinline__ double xpow(double x, double p, int ip) {
+  if (ip >= 0) {
+    double r = 1.0;
+    for (int k = 0; k < ip; ++k) r *= x;
+    return r;
+  }
+  return pow(x, p);
+}
+
+__global__ void modulus_kernel(Grid g, int n_phase, const double* __restrict__ x, PhaseTable ph,
+                               double penal, int ipenal, double* __restrict__ E64,
+                               __nv_bfloat16* __restrict__ Ebf) {
+  const long long n = (long long)g.nx * g.ny;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % g.nx), j = (int)(e / g.nx);
+    double E = 0.0;
+    for (int p = 0; p < n_phase; ++p) E += ph.E[p] * xpow(x[(long long)p * n + e], penal, ipenal);
+    const long long k = g.at(i, j);
+    E64[k] = E;
+    if (Ebf) Ebf[k] = __double2bfloat16(E);
+  }
+}
+
+__global__ void fine_invd_kernel(Grid g, const double* __restrict__ E, double w_over_kdiag,
+                                 double* __restrict__ invd1) {
+  const long long n = (long long)(g.nx + 1) * (g.ny + 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+    const long long k = g.at(i, j);
+    double d = 0.0;
+    if (!g.is_fixed(i, j)) {
+      const double se = ((E[k - g.pitch - 1] + E[k - g.pitch]) + E[k - 1]) + E[k];
+      d = w_over_kdiag / se;
+    }
+    invd1[k] = d;
+  }
+}
+
+// Moments M_ab = <E xi^a eta^b> (a + b <= 2) of a parent element from its four
+// children, each child mapped by xi = (xi' + sx) / 2, eta = (eta' + sy) / 2.
+struct Mom {
+  double m00, m10, m01, m20, m02, m11;
+};
+
+__device__ __forceinline__ void accum_child(Mom& P, const Mom& c, double sx, double sy) {
+  P.m00 += 0.25 * c.m00;
+  P.m10 += 0.125 * (c.m10 + sx * c.m00);
+  P.m01 += 0.125 * (c.m01 + sy * c.m00);
+  P.m20 += 0.0625 * (c.m20 + 2.0 * sx * c.m10 + c.m00);
+  P.m02 += 0.0625 * (c.m02 + 2.0 * sy * c.m01 + c.m00);
+  P.m11 += 0.0625 * (c.m11 + sy * c.m10 + sx * c.m01 + sx * sy * c.m00);
+}
+
+__device__ __forceinline__ void store_mom(double* mom, long long stride, long long k, const Mom& M) {
+  mom[0 * stride + k] = M.m00;
+  mom[1 * stride + k] = M.m10;
+  mom[2 * stride + k] = M.m01;
+  mom[3 * stride + k] = M.m20;
+  mom[4 * stride + k] = M.m02;
+  mom[5 * stride + k] = M.m11;
+}
+
+__global__ void moments_from_fine_kernel(Grid gc, Grid gf, const double* __restrict__ E64,
+                                         const __nv_bfloat16* __restrict__ Ebf, int redisc,
+                                         double* __restrict__ mom) {
+  const long long n = (long long)gc.nx * gc.ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % gc.nx), J = (int)(t / gc.nx);
+    Mom P = {0, 0, 0, 0, 0, 0};
+    double Emean = 0.0;
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        const long long kf = gf.at(2 * I + cx, 2 * J + cy);
+        const double E = Ebf ? (double)__bfloat162float(Ebf[kf]) : E64[kf];
+        const Mom c = {E, 0.0, 0.0, E / 3.0, E / 3.0, 0.0};
+        accum_child(P, c, 2.0 * cx - 1.0, 2.0 * cy - 1.0);
+        Emean += 0.25 * E;
+      }
+    if (redisc) P = {Emean, 0.0, 0.0, Emean / 3.0, Emean / 3.0, 0.0};
+    store_mom(mom, gc.size(), gc.at(I, J), P);
+  }
+}
+
+__global__ void moments_from_coarse_kernel(Grid gc, Grid gf, const double* __restrict__ momf,
+                                           int redisc, double* __restrict__ momc) {
+  const long long n = (long long)gc.nx * gc.ny;
+  const long long sf = gf.size();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % gc.nx), J = (int)(t / gc.nx);
+    Mom P = {0, 0, 0, 0, 0, 0};
+    double Emean = 0.0;
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        const long long kf = gf.at(2 * I + cx, 2 * J + cy);
+        const Mom c = {momf[kf], momf[sf + kf], momf[2 * sf + kf],
+                       momf[3 * sf + kf], momf[4 * sf + kf], momf[5 * sf + kf]};
+        accum_child(P, c, 2.0 * cx - 1.0, 2.0 * cy - 1.0);
+        Emean += 0.25 * c.m00;
+      }
+    if (redisc) P = {Emean, 0.0, 0.0, Emean / 3.0, Emean / 3.0, 0.0};
+    store_mom(momc, gc.size(), gc.at(I, J), P);
+  }
+}
+
+template <typename T>
+__global__ void coefs_kernel(Grid g, const double* __restrict__ mom, double nu, T* __restrict__ coef) {
+  const long long n = (long long)g.nx * g.ny;
+  const long long s = g.size();
+  const double kap = 1.0 / (4.0 * (1.0 - nu * nu)), gs = 0.5 * (1.0 - nu);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % g.nx), J = (int)(t / g.nx);
+    const long long k = g.at(I, J);
+    const double M00 = mom[k], M10 = mom[s + k], M01 = mom[2 * s + k];
+    const double M20 = mom[3 * s + k], M02 = mom[4 * s + k], M11 = mom[5 * s + k];
+    const double A[NCOEF] = {kap * M00,           kap * M01,       kap * (M02 + gs * M20),
+                             kap * M00,           kap * M10,       kap * (M20 + gs * M02),
+                             kap * nu * M00,      kap * nu * M10,  kap * nu * M01,
+                             kap * (nu + gs) * M11, kap * gs * M00, kap * gs * M10,
+                             kap * gs * M01};
+#pragma unroll
+    for (int c = 0; c < NCOEF; ++c) coef[c * s + k] = (T)A[c];
+  }
+}
+
+// Diagonal of an element matrix J^T A J at local node q (0 BL, 1 BR, 2 TR, 3 TL):
+// J column of u_x at q is (s1, s3, 0, 0, s2), of u_y is (0, 0, s2, s3, s1), with
+// s1 = (-1, 1, 1, -1), s2 = (-1, -1, 1, 1), s3 = (1, -1, 1, -1); s1 s3 = s2, s2 s3 = s1.
+template <typename T>
+__device__ __forceinline__ void elem_diag(const T* coef, long long s, long long k, int q, double& dx,
+                                          double& dy) {
+  const double s1 = (q == 1 || q == 2) ? 1.0 : -1.0;
+  const double s2 = (q >= 2) ? 1.0 : -1.0;
+  const double A0 = coef[k], A1 = coef[s + k], A2 = coef[2 * s + k], A3 = coef[3 * s + k];
+  const double A4 = coef[4 * s + k], A5 = coef[5 * s + k], A10 = coef[10 * s + k];
+  const double A11 = coef[11 * s + k], A12 = coef[12 * s + k];
+  dx += A0 + A2 + A10 + 2.0 * s2 * A1 + 2.0 * s1 * A11;
+  dy += A3 + A5 + A10 + 2.0 * s1 * A4 + 2.0 * s2 * A12;
+}
+
+template <typename T>
+__global__ void coarse_invd_kernel(Grid g, const T* __restrict__ coef, double omega,
+                                   typename V2<T>::t* __restrict__ invd2) {
+  const long long n = (long long)(g.nx + 1) * (g.ny + 1);
+  const long long s = g.size();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
+    const long long k = g.at(i, j);
+    typename V2<T>::t out = mk2<T>(T(0), T(0));
+    if (!g.is_fixed(i, j)) {
+      double dx = 0.0, dy = 0.0;
+      // Ghost elements have zero coefficients, so all four may be visited.
+      elem_diag(coef, s, k - g.pitch - 1, 2, dx, dy);  // element (i-1, j-1): node is TR
+      elem_diag(coef, s, k - g.pitch, 3, dx, dy);      // element (i, j-1): TL
+      elem_diag(coef, s, k - 1, 1, dx, dy);            // element (i-1, j): BR
+      elem_diag(coef, s, k, 0, dx, dy);                // element (i, j): BL
+      out = mk2<T>(T(omega / dx), T(omega / dy));
+    }
+    invd2[k] = out;
+  }
+}
+
+// Row r of the dense coarsest matrix: DOF (node (i, j), component c).
+__global__ void dense_assemble_kernel(Grid g, const double* __restrict__ coef,
+                                      const int* __restrict__ dof_index, int n,
+                                      double* __restrict__ Kd) {
+  const long long s = g.size();
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    // Find the node of row r: scan is avoided by storing the inverse map in
+    // dof_index's second half (2 * g.size() .. + n).
+    const int sidx = dof_index[2 * s + r];
+    const long long k = sidx >> 1;
+    const int c = sidx & 1;
+    const int j = (int)(k / g.pitch) - 1, i = (int)(k % g.pitch) - OFFX;
+    double* row = Kd + (long long)r * n;
+    const int ei[4] = {i - 1, i, i - 1, i}, ej[4] = {j - 1, j - 1, j, j}, eq[4] = {2, 3, 1, 0};
+    for (int t = 0; t < 4; ++t) {
+      if (ei[t] < 0 || ei[t] >= g.nx || ej[t] < 0 || ej[t] >= g.ny) continue;
+      const long long ke = g.at(ei[t], ej[t]);
+      double A[5][5] = {};
+      A[0][0] = coef[ke];
+      A[0][1] = A[1][0] = coef[s + ke];
+      A[1][1] = coef[2 * s + ke];
+      A[2][2] = coef[3 * s + ke];
+      A[2][3] = A[3][2] = coef[4 * s + ke];
+      A[3][3] = coef[5 * s + ke];
+      A[0][2] = A[2][0] = coef[6 * s + ke];
+      A[0][3] = A[3][0] = coef[7 * s + ke];
+      A[1][2] = A[2][1] = coef[8 * s + ke];
+      A[1][3] = A[3][1] = coef[9 * s + ke];
+      A[4][4] = coef[10 * s + ke];
+      A[1][4] = A[4][1] = coef[11 * s + ke];
+      A[3][4] = A[4][3] = coef[12 * s + ke];
+      // J column of this row's DOF.
+      const int q = eq[t];
+      const double s1 = (q == 1 || q == 2) ? 1.0 : -1.0, s2 = (q >= 2) ? 1.0 : -1.0;
+      const double s3 = s1 * s2;  // s1 s2 = s3 (see elem_diag)
+      double ja[5];
+      if (c == 0) { ja[0] = s1; ja[1] = s3; ja[2] = 0; ja[3] = 0; ja[4] = s2; }
+      else { ja[0] = 0; ja[1] = 0; ja[2] = s2; ja[3] = s3; ja[4] = s1; }
+      double Aj[5];
+      for (int m = 0; m < 5; ++m) {
+        Aj[m] = 0.0;
+        for (int l = 0; l < 5; ++l) Aj[m] += A[m][l] * ja[l];
+      }
+      // Element nodes: BL (ei, ej), BR, TR, TL.
+      const int ni[4] = {ei[t], ei[t] + 1, ei[t] + 1, ei[t]}, nj[4] = {ej[t], ej[t], ej[t] + 1, ej[t] + 1};
+      for (int m = 0; m < 4; ++m) {
+        const double t1 = (m == 1 || m == 2) ? 1.0 : -1.0, t2 = (m >= 2) ? 1.0 : -1.0;
+        const double t3 = t1 * t2;
+        const long long kn = g.at(ni[m], nj[m]);
+        const double ex = Aj[0] * t1 + Aj[1] * t3 + Aj[4] * t2;  // u_x column of node m
+        const double ey = Aj[2] * t2 + Aj[3] * t3 + Aj[4] * t1;  // u_y column
+        const int cx = dof_index[2 * kn], cy = dof_index[2 * kn + 1];
+        if (cx >= 0) row[cx] += ex;
+        if (cy >= 0) row[cy] += ey;
+      }
+    }
+  }
+}
+
+constexpr int CHOL_NT = 512;
+
+// Right-looking Cholesky (Alg. 3, textbook indices) restricted to the band
+// |i - j| <= bw of the lower triangle, one block.
+__global__ void __launch_bounds__(CHOL_NT) cholesky_band_kernel(int n, int bw, double* A, int* err) {
+  extern __shared__ short2 pairs[];  // (row, col) offsets of the trailing triangle
+  __shared__ double piv;
+  const int npmax = bw * (bw + 1) / 2;
+  for (int ii = threadIdx.x; ii < bw; ii += CHOL_NT)
+    for (int jj = 0; jj <= ii; ++jj) pairs[ii * (ii + 1) / 2 + jj] = make_short2((short)ii, (short)jj);
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      double d = A[(long long)k * n + k];
+      if (!(d > 0.0) || !(d < 1.0e300)) {
+        *err = 1;
+        d = 1.0;
+      }
+      d = sqrt(d);
+      A[(long long)k * n + k] = d;
+      piv = d;
+    }
+    __syncthreads();
+    const int last = min(n - 1, k + bw);
+    for (int i = k + 1 + threadIdx.x; i <= last; i += CHOL_NT) A[(long long)i * n + k] /= piv;
+    __syncthreads();
+    const int m = last - k;
+    const int np = m * (m + 1) / 2;
+    for (int t = threadIdx.x; t < np && t < npmax; t += CHOL_NT) {
+      const short2 pr = pairs[t];
+      const int i = k + 1 + pr.x, j = k + 1 + pr.y;
+      A[(long long)i * n + j] -= A[(long long)i * n + k] * A[(long long)j * n + k];
+    }
+    __syncthreads();
+  }
+}
+
+// Column j of K_0^-1 (= row j, by symmetry): L y = e_j, then L^T x = y, with
+// row j of Kinv as the workspace.  One warp per column.
+__global__ void inverse_kernel(int n, int bw, const double* __restrict__ L, double* __restrict__ Kinv) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  double* y = Kinv + (long long)j * n;
+  for (int i = lane; i < j; i += 32) y[i] = 0.0;
+  __syncwarp();
+  for (int i = j; i < n; ++i) {
+    double s = 0.0;
+    const int k0 = max(j, i - bw);
+    for (int k = k0 + lane; k < i; k += 32) s += L[(long long)i * n + k] * y[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = ((i == j ? 1.0 : 0.0) - s) / L[(long long)i * n + i];
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = 0.0;
+    const int k1 = min(n - 1, i + bw);
+    for (int k = i + 1 + lane; k <= k1; k += 32) s += L[(long long)k * n + i] * y[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = (y[i] - s) / L[(long long)i * n + i];
+    __syncwarp();
+  }
+}
+
+__global__ void sensitivity_kernel(int nelx, int nely, int n_phase, const double* __restrict__ x,
+                                   PhaseTable ph, double penal, int ipenal, FineConst<double> kf,
+                                   const double* __restrict__ u, double* __restrict__ dcdx,
+                                   int accumulate) {
+  const long long n = (long long)nelx * nely;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nelx), j = (int)(e / nelx);
+    const long long n0 = (long long)j * (nelx + 1) + i, n3 = n0 + nelx + 1;
+    const double2 bl = make_double2(u[2 * n0], u[2 * n0 + 1]);
+    const double2 br = make_double2(u[2 * n0 + 2], u[2 * n0 + 3]);
+    const double2 tr = make_double2(u[2 * n3 + 2], u[2 * n3 + 3]);
+    const double2 tl = make_double2(u[2 * n3], u[2 * n3 + 1]);
+    const Strain<double> w = strain_coords<double>(bl, br, tr, tl);
+    const Strain<double> t = fine_core<double>(w, 1.0, kf);
+    const double we = w.c1 * t.c1 + w.c3 * t.c3 + w.d2 * t.d2 + w.d3 * t.d3 + w.s * t.s;
+    for (int p = 0; p < n_phase; ++p) {
+      const long long k = (long long)p * n + e;
+      const double g = -penal * xpow(x[k], penal - 1.0, ipenal >= 1 ? ipenal - 1 : -1) * ph.E[p] * we;
+      dcdx[k] = accumulate ? dcdx[k] + g : g;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+static int blocks_for(long long n, int num_sms) {
+  long long b = (n + 255) / 256;
+  const long long cap = (long long)num_sms * 8;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+cudaError_t launch_modulus(const Grid& g, int n_phase, const double* x, PhaseTable ph, double penal,
+                           int ipenal, double* E64, __nv_bfloat16* Ebf, cudaStream_t s, int num_sms) {
+  modulus_kernel<<<blocks_for((long long)g.nx * g.ny, num_sms), 256, 0, s>>>(g, n_phase, x, ph, penal,
+                                                                             ipenal, E64, Ebf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_invd(const Grid& g, const double* E64, double w_over_kdiag, double* invd1,
+                             cudaStream_t s, int num_sms) {
+  fine_invd_kernel<<<blocks_for((long long)(g.nx + 1) * (g.ny + 1), num_sms), 256, 0, s>>>(
+      g, E64, w_over_kdiag, invd1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_from_fine(const Grid& gc, const Grid& gf, const double* E64,
+                                     const __nv_bfloat16* Ebf, int rediscretize, double* mom,
+                                     cudaStream_t s, int num_sms) {
+  moments_from_fine_kernel<<<blocks_for((long long)gc.nx * gc.ny, num_sms), 256, 0, s>>>(
+      gc, gf, E64, Ebf, rediscretize, mom);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_from_coarse(const Grid& gc, const Grid& gf, const double* momf,
+                                       int rediscretize, double* momc, cudaStream_t s, int num_sms) {
+  moments_from_coarse_kernel<<<blocks_for((long long)gc.nx * gc.ny, num_sms), 256, 0, s>>>(
+      gc, gf, momf, rediscretize, momc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coefs(const Grid& g, const double* mom, double nu, T* coef, cudaStream_t s,
+                         int num_sms) {
+  coefs_kernel<T><<<blocks_for((long long)g.nx * g.ny, num_sms), 256, 0, s>>>(g, mom, nu, coef);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coefs<double>(const Grid&, const double*, double, double*, cudaStream_t, int);
+template cudaError_t launch_coefs<float>(const Grid&, const double*, double, float*, cudaStream_t, int);
+
+template <typename T>
+cudaError_t launch_coarse_invd(const Grid& g, const T* coef, double omega,
+                               typename V2<T>::t* invd2, cudaStream_t s, int num_sms) {
+  coarse_invd_kernel<T><<<blocks_for((long long)(g.nx + 1) * (g.ny + 1), num_sms), 256, 0, s>>>(
+      g, coef, omega, invd2);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_invd<double>(const Grid&, const double*, double, double2*,
+                                                cudaStream_t, int);
+template cudaError_t launch_coarse_invd<float>(const Grid&, const float*, double, float2*,
+                                               cudaStream_t, int);
+
+cudaError_t launch_dense_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
+                                  double* Kd, cudaStream_t s) {
+  dense_assemble_kernel<<<(n + 127) / 128, 128, 0, s>>>(g, coef64, dof_index, n, Kd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_inverse(int n, int bw, double* Kd, double* Kinv, int* err_flag,
+                                    cudaStream_t s, int num_sms) {
+  (void)num_sms;
+  const size_t smem = sizeof(short2) * (size_t)bw * (bw + 1) / 2 + 16;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(cholesky_band_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  cholesky_band_kernel<<<1, CHOL_NT, smem, s>>>(n, bw, Kd, err_flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  inverse_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, bw, Kd, Kinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensitivity(int nelx, int nely, int n_phase, const double* x, PhaseTable ph,
+                               double penal, int ipenal, FineConst<double> kf, const double* u,
+                               double* dcdx, int accumulate, cudaStream_t s, int num_sms) {
+  sensitivity_kernel<<<blocks_for((long long)nelx * nely, num_sms), 256, 0, s>>>(
+      nelx, nely, n_phase, x, ph, penal, ipenal, kf, u, dcdx, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace mto

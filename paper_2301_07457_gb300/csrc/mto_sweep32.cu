@@ -1,0 +1,46 @@
+// float32 instantiations of the marching sweeps (mixed-precision V-cycle:
+// finest level with bfloat16 moduli, coarse levels with float32 element
+// matrices).
+#include "mto_launch.h"
+
+namespace mto {
+
+template <int SRC, int MODE, bool DOT>
+static cudaError_t go(const SweepParams<float>& p, const SweepShape& sh, cudaStream_t s) {
+  sweep_kernel<float, SRC, MODE, DOT, float2><<<sh.nblocks, SWEEP_NT, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepParams<float> p,
+                                const SweepShape& sh, cudaStream_t s) {
+  (void)zfloat;
+  p.nstrips = sh.nstrips;
+  p.nchunks = sh.nchunks;
+  p.H = sh.H;
+  if (src == SRC_FINEBF) {
+    switch (mode) {
+      case MODE_APPLY: return go<SRC_FINEBF, MODE_APPLY, false>(p, sh, s);
+      case MODE_SMOOTH:
+        return dot ? go<SRC_FINEBF, MODE_SMOOTH, true>(p, sh, s)
+                   : go<SRC_FINEBF, MODE_SMOOTH, false>(p, sh, s);
+      case MODE_PSMOOTH:
+        return dot ? go<SRC_FINEBF, MODE_PSMOOTH, true>(p, sh, s)
+                   : go<SRC_FINEBF, MODE_PSMOOTH, false>(p, sh, s);
+      case MODE_RESTRICT: return go<SRC_FINEBF, MODE_RESTRICT, false>(p, sh, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (src == SRC_COARSE) {
+    switch (mode) {
+      case MODE_APPLY: return go<SRC_COARSE, MODE_APPLY, false>(p, sh, s);
+      case MODE_SMOOTH: return go<SRC_COARSE, MODE_SMOOTH, false>(p, sh, s);
+      case MODE_PSMOOTH: return go<SRC_COARSE, MODE_PSMOOTH, false>(p, sh, s);
+      case MODE_RESTRICT: return go<SRC_COARSE, MODE_RESTRICT, false>(p, sh, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mto

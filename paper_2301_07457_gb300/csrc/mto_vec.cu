@@ -1,0 +1,284 @@
+// Pointwise kernels of the PCG recurrence (Alg. 2), the first smoothing sweep
+// from a zero iterate (Sec. 2.3 with x_0 = 0), layout conversions and the
+// coarsest-grid solve of Alg. 1 (l = 0) as a dense product with K_0^-1.
+#include "mto_launch.h"
+
+namespace mto {
+
+int vec_blocks(long long n, int num_sms) {
+  long long b = (n + VEC_NT - 1) / VEC_NT;
+  const long long cap = (long long)num_sms * 8;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+__device__ __forceinline__ void node_of(const Grid& g, long long k, int& i, int& j) {
+  j = (int)(k / g.pitch) - 1;
+  i = (int)(k - (long long)(j + 1) * g.pitch) - OFFX;
+}
+
+__device__ __forceinline__ bool stop_now(const DevScalars* sc) {
+  return sc != nullptr && sc->done != RUNNING;
+}
+
+__global__ void jacobi0_fine64_kernel(Grid g, const double* __restrict__ invd1,
+                                      const double2* __restrict__ r, double2* __restrict__ z,
+                                      const DevScalars* sc) {
+  if (stop_now(sc)) return;
+  const long long n = g.size();
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    node_of(g, k, i, j);
+    double2 out = make_double2(0.0, 0.0);
+    if (g.active(i, j)) {
+      const double d = invd1[k];
+      const double2 rr = r[k];
+      out = make_double2(d * rr.x, d * rr.y);
+    }
+    z[k] = out;
+  }
+}
+
+__global__ void jacobi0_finebf_kernel(Grid g, const __nv_bfloat16* __restrict__ E, float wdiag,
+                                      const double2* __restrict__ r, float2* __restrict__ r32,
+                                      float2* __restrict__ z, const DevScalars* sc) {
+  if (stop_now(sc)) return;
+  const long long n = g.size();
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    node_of(g, k, i, j);
+    const double2 rr = r[k];
+    const float2 rf = make_float2((float)rr.x, (float)rr.y);
+    float2 out = make_float2(0.f, 0.f);
+    if (g.active(i, j)) {
+      const float se = __bfloat162float(E[k]) + __bfloat162float(E[k - 1]) +
+                       __bfloat162float(E[k - g.pitch]) + __bfloat162float(E[k - g.pitch - 1]);
+      const float d = wdiag / se;
+      out = make_float2(d * rf.x, d * rf.y);
+    }
+    r32[k] = rf;
+    z[k] = out;
+  }
+}
+
+template <typename T>
+__global__ void jacobi0_coarse_kernel(Grid g, const typename V2<T>::t* __restrict__ invd2,
+                                      const typename V2<T>::t* __restrict__ b,
+                                      typename V2<T>::t* __restrict__ z, const DevScalars* sc) {
+  if (stop_now(sc)) return;
+  const long long n = g.size();
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    node_of(g, k, i, j);
+    typename V2<T>::t out = mk2<T>(T(0), T(0));
+    if (g.active(i, j)) {
+      const typename V2<T>::t d = invd2[k], bb = b[k];
+      out = mk2<T>(d.x * bb.x, d.y * bb.y);
+    }
+    z[k] = out;
+  }
+}
+
+__global__ void __launch_bounds__(VEC_NT)
+    update_kernel(long long n, double2* __restrict__ x, double2* __restrict__ r,
+                  const double2* __restrict__ p, const double2* __restrict__ q, double* partials,
+                  unsigned* ticket, DevScalars* sc) {
+  if (sc->done != RUNNING) return;
+  const double alpha = sc->alpha;
+  double acc = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double2 pp = p[k], qq = q[k];
+    double2 xx = x[k], rr = r[k];
+    xx.x += alpha * pp.x;
+    xx.y += alpha * pp.y;
+    rr.x -= alpha * qq.x;
+    rr.y -= alpha * qq.y;
+    x[k] = xx;
+    r[k] = rr;
+    acc += rr.x * rr.x + rr.y * rr.y;
+  }
+  block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, FIN_UPDATE, nullptr);
+}
+
+__global__ void __launch_bounds__(VEC_NT)
+    dot_kernel(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
+               double* partials, unsigned* ticket, DevScalars* sc, int finish, double* out_value) {
+  double acc = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double2 x = a[k], y = b[k];
+    acc += x.x * y.x + x.y * y.y;
+  }
+  block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, finish, out_value);
+}
+
+__global__ void pack_kernel(Grid g, const double* __restrict__ src, double2* __restrict__ dst) {
+  const long long n = g.size();
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    node_of(g, k, i, j);
+    double2 v = make_double2(0.0, 0.0);
+    if (g.active(i, j)) {
+      const long long s = 2 * ((long long)j * (g.nx + 1) + i);
+      v = make_double2(src[s], src[s + 1]);
+    }
+    dst[k] = v;
+  }
+}
+
+__global__ void unpack_kernel(Grid g, const double2* __restrict__ src, double* __restrict__ dst) {
+  const long long n = (long long)(g.nx + 1) * (g.ny + 1);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(k % (g.nx + 1)), j = (int)(k / (g.nx + 1));
+    const double2 v = src[g.at(i, j)];
+    dst[2 * k] = v.x;
+    dst[2 * k + 1] = v.y;
+  }
+}
+
+__global__ void pack_f32_kernel(Grid g, const double* __restrict__ src, float2* __restrict__ dst) {
+  const long long n = g.size();
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    node_of(g, k, i, j);
+    float2 v = make_float2(0.f, 0.f);
+    if (g.active(i, j)) {
+      const long long s = 2 * ((long long)j * (g.nx + 1) + i);
+      v = make_float2((float)src[s], (float)src[s + 1]);
+    }
+    dst[k] = v;
+  }
+}
+
+__global__ void unpack_f32_kernel(Grid g, const float2* __restrict__ src, double* __restrict__ dst) {
+  const long long n = (long long)(g.nx + 1) * (g.ny + 1);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(k % (g.nx + 1)), j = (int)(k / (g.nx + 1));
+    const float2 v = src[g.at(i, j)];
+    dst[2 * k] = v.x;
+    dst[2 * k + 1] = v.y;
+  }
+}
+
+__global__ void unpack_elems_kernel(Grid g, const double* __restrict__ src, double* __restrict__ dst) {
+  const long long n = (long long)g.nx * g.ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    dst[k] = src[g.at((int)(k % g.nx), (int)(k / g.nx))];
+  }
+}
+
+// One warp per row of K_0^-1; every block stages the free coarse right-hand
+// side in shared memory first.  free_idx[k] = scalar index (2 * node offset +
+// component) of free DOF k in the padded level array.
+constexpr int GEMV_NT = 256;
+constexpr int GEMV_MAXN = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(GEMV_NT)
+    coarsest_gemv_kernel(int n, const int* __restrict__ free_idx, const double* __restrict__ Kinv,
+                         const T* __restrict__ b, T* __restrict__ z, const DevScalars* sc) {
+  if (stop_now(sc)) return;
+  extern __shared__ double bs[];
+  for (int k = threadIdx.x; k < n; k += GEMV_NT) bs[k] = (double)b[free_idx[k]];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (GEMV_NT / 32) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const double* kr = Kinv + (long long)row * n;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc += kr[k] * bs[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) z[free_idx[row]] = (T)acc;
+}
+
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_jacobi0_fine64(const Grid& g, const double* invd1, const double2* r, double2* z,
+                                  DevScalars* sc, int nblocks, cudaStream_t s) {
+  jacobi0_fine64_kernel<<<nblocks, VEC_NT, 0, s>>>(g, invd1, r, z, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi0_finebf(const Grid& g, const __nv_bfloat16* E, float wdiag,
+                                  const double2* r, float2* r32, float2* z, DevScalars* sc,
+                                  int nblocks, cudaStream_t s) {
+  jacobi0_finebf_kernel<<<nblocks, VEC_NT, 0, s>>>(g, E, wdiag, r, r32, z, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jacobi0_coarse(const Grid& g, const typename V2<T>::t* invd2,
+                                  const typename V2<T>::t* b, typename V2<T>::t* z,
+                                  DevScalars* sc, int nblocks, cudaStream_t s) {
+  jacobi0_coarse_kernel<T><<<nblocks, VEC_NT, 0, s>>>(g, invd2, b, z, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_jacobi0_coarse<double>(const Grid&, const double2*, const double2*,
+                                                   double2*, DevScalars*, int, cudaStream_t);
+template cudaError_t launch_jacobi0_coarse<float>(const Grid&, const float2*, const float2*,
+                                                  float2*, DevScalars*, int, cudaStream_t);
+
+cudaError_t launch_update(const Grid& g, double2* x, double2* r, const double2* p, const double2* q,
+                          double* partials, unsigned* ticket, DevScalars* sc, int nblocks,
+                          cudaStream_t s) {
+  update_kernel<<<nblocks, VEC_NT, 0, s>>>(g.size(), x, r, p, q, partials, ticket, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* partials,
+                       unsigned* ticket, DevScalars* sc, int finish, double* out_value,
+                       int nblocks, cudaStream_t s) {
+  dot_kernel<<<nblocks, VEC_NT, 0, s>>>(n, a, b, partials, ticket, sc, finish, out_value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms) {
+  pack_kernel<<<vec_blocks(g.size(), num_sms), VEC_NT, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack(const Grid& g, const double2* src, double* dst, cudaStream_t s, int num_sms) {
+  unpack_kernel<<<vec_blocks((long long)(g.nx + 1) * (g.ny + 1), num_sms), VEC_NT, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack_f32(const Grid& g, const double* src, float2* dst, cudaStream_t s, int num_sms) {
+  pack_f32_kernel<<<vec_blocks(g.size(), num_sms), VEC_NT, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack_f32(const Grid& g, const float2* src, double* dst, cudaStream_t s, int num_sms) {
+  unpack_f32_kernel<<<vec_blocks((long long)(g.nx + 1) * (g.ny + 1), num_sms), VEC_NT, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_elems(const Grid& g, const double* src, double* dst, cudaStream_t s,
+                                int num_sms) {
+  unpack_elems_kernel<<<vec_blocks((long long)g.nx * g.ny, num_sms), VEC_NT, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, const double* Kinv,
+                                 const typename V2<T>::t* b, typename V2<T>::t* z,
+                                 DevScalars* sc, cudaStream_t s) {
+  (void)g;
+  if (n > GEMV_MAXN) return cudaErrorInvalidValue;
+  const int blocks = (n + GEMV_NT / 32 - 1) / (GEMV_NT / 32);
+  coarsest_gemv_kernel<T><<<blocks, GEMV_NT, n * sizeof(double), s>>>(
+      n, free_idx, Kinv, reinterpret_cast<const T*>(b), reinterpret_cast<T*>(z), sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarsest_gemv<double>(const Grid&, int, const int*, const double*,
+                                                  const double2*, double2*, DevScalars*, cudaStream_t);
+template cudaError_t launch_coarsest_gemv<float>(const Grid&, int, const int*, const double*,
+                                                 const float2*, float2*, DevScalars*, cudaStream_t);
+
+}  // namespace mto

@@ -1,0 +1,66 @@
+"""The C ABI library builds, loads without a GPU, and exports every declared symbol."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mto.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mto_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2301_07457_gb300.build import build
+    try:
+        return build()
+    except RuntimeError as e:  # no nvcc on this machine
+        pytest.skip(str(e))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mto_create_mesh", "mto_set_design", "mto_solve", "mto_compliance_grad",
+                     "mto_destroy", "mto_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (mto_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches(libpath):
+    from paper_2301_07457_gb300 import _lib
+    lib = _lib.load()
+    assert set(_lib.SIGNATURES) == set(declared_functions())
+    assert lib.mto_status_string(0) == b"ok"
+    assert lib.mto_status_string(5) == b"not converged"
+    o = _lib.default_opts()
+    assert (o.tol, o.max_it, o.omega, o.nu1, o.nu2, o.n_coarsen) == (1e-8, 500, 0.6, 2, 2, 3)
+
+
+def test_argument_validation_needs_no_gpu(libpath):
+    import ctypes
+    from paper_2301_07457_gb300 import _lib
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    o = _lib.default_opts()
+    # Rejected before any CUDA call: bad sizes, no clamped edge, bad options.
+    assert lib.mto_create_mesh(ctypes.byref(h), 0, 8, 0.3, 1, ctypes.byref(o), 0, None) == _lib.ERR_ARG
+    assert lib.mto_create_mesh(ctypes.byref(h), 8, 8, 0.3, 0, ctypes.byref(o), 0, None) == _lib.ERR_ARG
+    assert lib.mto_create_mesh(ctypes.byref(h), 12, 8, 0.3, 1, ctypes.byref(o), 0, None) == \
+        _lib.ERR_UNSUPPORTED_MESH
+    o.omega = 1.5
+    assert lib.mto_create_mesh(ctypes.byref(h), 8, 8, 0.3, 1, ctypes.byref(o), 0, None) == _lib.ERR_ARG
+    assert lib.mto_solve(None, 1, None, None, None) == _lib.ERR_ARG
+    assert lib.mto_create_mesh(None, 8, 8, 0.3, 1, None, 0, None) == _lib.ERR_ARG
