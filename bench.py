@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the pCGMG solve on GB300: one JSON line on stdout.
+
+Step = one pass of the whole hot path on the 2048 x 2048 Q4 square wall:
+mto_set_design (moduli, coarse operators, coarsest inverse) + mto_solve
+(mixed-precision pCGMG to a 1e-8 relative residual) + mto_compliance_grad
+(compliance and sensitivities).  value = solves/s over all ranks.
+
+--impl reference times the CPU oracle instead (a bounded sample of the same
+workload on the host cores).  Under torchrun every rank runs its own
+independent solves (weak scaling, no collective on the data path).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pCGMG solves/s and GDOF-iter/s at 2048² Q4, mixed vs FP64, to 1e-8 residual; HBM % peak"
+UNIT = "solves/s"
+EP = [1.0, 0.5, 0.25, 1e-9]
+PENAL = 3.0
+SEED = 0
+# Algorithmic work per finest-level node of the two timed kernels:
+#  * outer sweep p = z + beta p, q = K p, p.q in float64: 48 FP64 pipe
+#    operations (15 strain-coordinate add/sub, 11 core mul/fma, 12 force add/sub,
+#    6 node-assembly adds, 2 fma for p, 2 fma for the dot);
+#  * float32 damped-Jacobi sweep: reads z (8 B) and b (8 B), the element's
+#    bf16 modulus (2 B), writes z (8 B): 26 B.
+KP_OPS_PER_NODE = 48
+SMOOTH32_BYTES_PER_NODE = 26
+SMOOTH64_OPS_PER_NODE = 48
+# FP64 pipe: 2 operations per clock per SM (1.25 TFLOP/s nominal at 2 flops
+# per FMA), 152 SMs, 2070 MHz.
+FP64_OPS_PEAK = 2 * 152 * 2.070e9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--n-coarsen", type=int, default=7)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-size", type=int, default=512)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [t.strip() for t in line.split(",")]
+                if len(p) >= 7:
+                    rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[0]) for r in rows if r[0].replace(".", "").isdigit())
+        smax = max(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure; only this leg of the bench uses it)
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import solver
+from synth import dirichlet_design, load_top_edge
+n, nc, budget, reps = {n}, {nc}, {budget}, {reps}
+x = dirichlet_design(n, n, 4, {seed}); f = load_top_edge(n, n)
+times, iters = [], []
+t_all = time.perf_counter()
+while True:
+    t = time.perf_counter()
+    r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol=1e-8)
+    times.append(time.perf_counter() - t); iters.append(r["iters"])
+    if (reps and len(times) >= reps) or (not reps and time.perf_counter() - t_all >= budget):
+        break
+print(json.dumps({{"times": times, "iters": iters}}))
+"""
+
+
+def oracle_sample(n, reps=0, budget=10.0):
+    nc = max(1, n.bit_length() - 1 - 4)  # coarsest 16 x 16, as at 2048^2 with 7 coarsenings
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, nc=nc, budget=budget, reps=reps, seed=SEED, ep=EP,
+                                 penal=PENAL)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    d["nc"] = nc
+    return d
+
+
+def ndof(n):
+    return 2 * (n + 1) * (n + 1)
+
+
+def cpu_value(d, n_sample, n_full):
+    # solves/s at the full size, scaled from the sample by the DOF ratio
+    # (pCGMG work per iteration is linear in DOFs; iteration counts are
+    # mesh-independent).
+    t = sum(d["times"]) / len(d["times"])
+    return (1.0 / t) * ndof(n_sample) / ndof(n_full)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_full, n_s = args.size, args.sample_size
+    for _ in range(args.warmup):
+        oracle_sample(n_s, reps=1)
+    d = oracle_sample(n_s, reps=max(1, args.steps))
+    v = cpu_value(d, n_s, n_full)
+    ms = 1000.0 * sum(d["times"]) / len(d["times"])
+    sample = (f"oracle pCGMG (numpy/scipy, FP64, 1 thread) on {n_s}x{n_s} (nc={d['nc']}), "
+              f"{len(d['times'])} solves, scaled to {n_full}^2 by the DOF ratio")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"pCGMG {n_full}x{n_full} Q4 square wall (oracle sample {n_s}^2)",
+                   "iters": d["iters"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2301_07457_gb300.build import build
+    build()
+    import paper_2301_07457_gb300 as mto
+    from paper_2301_07457_gb300 import _lib
+    from synth import dirichlet_design, load_top_edge
+
+    n, nc = args.size, args.n_coarsen
+    x_np = dirichlet_design(n, n, 4, SEED)
+    f_np = load_top_edge(n, n)
+    x = torch.from_numpy(x_np).to(dev)
+    f = torch.from_numpy(f_np).to(dev)
+    nodes = (n + 1) * (n + 1)
+    hbm_peak, peak_kind = peaks()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def launches(mesh):
+        c = ctypes.c_longlong()
+        _lib.check(mesh._lib.mto_get_launch_count(mesh._h, ctypes.byref(c)), "launch count")
+        return c.value
+
+    def step(mesh):
+        mesh.set_design(x, EP, PENAL)
+        u, st = mesh.solve(f)
+        C, g = mesh.compliance_grad(f, u)
+        return st, C
+
+    def timed(mesh, steps, warmup, timing=False):
+        for _ in range(warmup):
+            step(mesh)
+        if timing:
+            _lib.check(mesh._lib.mto_set_kernel_timing(mesh._h, 1), "timing")
+            step(mesh)  # rebuild the graph with event nodes outside the timed region
+            _lib.check(mesh._lib.mto_set_kernel_timing(mesh._h, 1), "timing reset")
+        torch.cuda.synchronize()
+        barrier()
+        l0 = launches(mesh)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        with ClockSampler(local) as clk:
+            e0.record()
+            for _ in range(steps):
+                st, C = step(mesh)
+                stats.append(st)
+            e1.record()
+            torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        kt = None
+        if timing:
+            avg = (ctypes.c_double * 2)()
+            cnt = (ctypes.c_longlong * 2)()
+            _lib.check(mesh._lib.mto_get_kernel_times(mesh._h, avg, cnt), "kernel times")
+            kt = {"ms": [avg[0], avg[1]], "samples": [cnt[0], cnt[1]]}
+        return ms, stats, launches(mesh) - l0, clk.summary(), kt
+
+    common = dict(n_coarsen=nc, tol=1e-8, max_it=1000, device=local)
+    mixed = mto.Mesh(n, n, precision="mixed", rr_every=25, flexible=True, **common)
+    ms, stats, nlaunch, clocks, kt = timed(mixed, args.steps, args.warmup, timing=True)
+    iters = [s["iters"] for s in stats]
+    solve_ms = [s["ms_solve"] for s in stats]
+    value = world * args.steps / (ms / 1000.0)
+    gdof = ndof(n) * sum(iters) / (ms / 1000.0) / 1e9
+    gdof_solve = ndof(n) * sum(iters) / (sum(solve_ms) / 1000.0) / 1e9
+
+    # Roofline of the two timed kernels (live CUDA events inside the solver graph).
+    kp_ms, sm_ms = kt["ms"]
+    kp_ops = KP_OPS_PER_NODE * nodes / (kp_ms / 1000.0)
+    sm_bytes = SMOOTH32_BYTES_PER_NODE * nodes / (sm_ms / 1000.0)
+    roofline = {"bound": "alu", "kernel": "outer sweep p=z+beta p, q=Kp, p.q (float64)",
+                "achieved": kp_ops / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-op/s",
+                "frac": kp_ops / FP64_OPS_PEAK, "traffic": None, "ms_per_launch": kp_ms,
+                "samples": kt["samples"][0],
+                "peak_kind": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
+    roofline_vcycle = {"bound": "hbm", "kernel": "finest damped-Jacobi sweep (float32, bf16 E)",
+                       "achieved": sm_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": sm_bytes / 1e9 / hbm_peak, "traffic": None, "ms_per_launch": sm_ms,
+                       "samples": kt["samples"][1], "peak_kind": peak_kind}
+
+    # FP64 path on the same input.
+    fp64 = None
+    if args.fp64_steps > 0:
+        m64 = mto.Mesh(n, n, precision="fp64", **common)
+        ms64, st64, _, clk64, kt64 = timed(m64, args.fp64_steps, 1, timing=True)
+        it64 = [s["iters"] for s in st64]
+        v64 = world * args.fp64_steps / (ms64 / 1000.0)
+        fp64 = {"solves_s": v64, "ms_per_step": ms64 / args.fp64_steps, "iters": it64,
+                "gdof_iter_s": ndof(n) * sum(it64) / (ms64 / 1000.0) / 1e9,
+                "rel_res_true": max(s["rel_res_true"] for s in st64),
+                "kernel_ms": kt64["ms"],
+                "smoother_fp64_frac_alu": SMOOTH64_OPS_PER_NODE * nodes / (kt64["ms"][1] / 1000.0) / FP64_OPS_PEAK,
+                "kp_fp64_frac_alu": KP_OPS_PER_NODE * nodes / (kt64["ms"][0] / 1000.0) / FP64_OPS_PEAK}
+        m64.close()
+
+    # End to end through the C ABI with pinned host buffers.
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x_np.shape, dtype=torch.float64, pin_memory=True)
+        xh.copy_(torch.from_numpy(x_np))
+        fh = torch.empty(f_np.shape, dtype=torch.float64, pin_memory=True)
+        fh.copy_(torch.from_numpy(f_np))
+        uh = torch.empty(f_np.shape, dtype=torch.float64, pin_memory=True)
+        gh = torch.empty(x_np.shape, dtype=torch.float64, pin_memory=True)
+        ch = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        Ep = (ctypes.c_double * 4)(*EP)
+        st = _lib.SolveStats()
+
+        def host_step():
+            code = mixed._lib.mto_run_host(mixed._h, 4, ctypes.c_void_p(xh.data_ptr()), Ep, PENAL, 1,
+                                           ctypes.c_void_p(fh.data_ptr()), ctypes.c_void_p(uh.data_ptr()),
+                                           ctypes.c_void_p(ch.data_ptr()), ctypes.c_void_p(gh.data_ptr()),
+                                           ctypes.byref(st))
+            _lib.check(code, "mto_run_host")
+
+        host_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": xh.numel() * 8 + fh.numel() * 8,
+               "d2h_bytes_per_step": uh.numel() * 8 + gh.numel() * 8 + 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        d = oracle_sample(args.sample_size, budget=10.0)
+        cpu = {"value": cpu_value(d, args.sample_size, n), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"oracle pCGMG (numpy/scipy FP64, 1 thread) on {args.sample_size}^2, "
+                          f"{len(d['times'])} solves ({sum(d['times']):.1f} s), iters {d['iters'][0]}, "
+                          f"scaled to {n}^2 by the DOF ratio")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"mixed pCGMG {n}x{n} Q4 square wall (3 solids + void, p=3, seeded "
+                               f"Dirichlet fractions), {nc} coarsenings to 16x16, tol 1e-8; step = "
+                               "set_design + solve + compliance/sensitivities",
+                   "nelx": n, "nely": n, "dofs": ndof(n), "n_coarsen": nc, "precision": "mixed",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (design 134 MB + load 67 MB read every step)"},
+        "gdof_iter_s": gdof, "gdof_iter_s_solve_only": gdof_solve, "iters": iters,
+        "rel_res_true_max": max(s["rel_res_true"] for s in stats),
+        "ms_setup": stats[-1]["ms_setup"], "ms_solve": solve_ms,
+        "fp64": fp64, "speedup_mixed_vs_fp64": (value / fp64["solves_s"]) if fp64 else None,
+        "roofline": roofline, "roofline_vcycle": roofline_vcycle,
+        "clocks": clocks, "gpu_launches": nlaunch, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    mixed.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -20,9 +20,11 @@
  * A CUDA failure inside a call returns MTO_ERR_CUDA and leaves the context
  * in a state where mto_destroy is still valid.
  *
- * Streams: all device work of a context is enqueued on the stream given at
- * creation.  Calls that return statistics to the host synchronise that
- * stream; all others only enqueue.
+ * Streams: the context runs its device work on a private stream that is
+ * ordered after the caller's stream (given at creation) on entry to every
+ * call, and before it on return.  mto_set_design, mto_solve, mto_run_host
+ * and mto_last_stats synchronise (the solve polls its convergence flag);
+ * mto_compliance_grad and the diagnostics only enqueue.
  *
  * Threads: a context is not thread-safe; use one context per host thread.
  */
@@ -106,11 +108,10 @@ mto_status mto_set_design(mto_ctx* ctx, int n_phase, const double* x_dev, const 
  * V-cycle (Alg. 1).  f_dev: device, float64 [n_rhs][nely+1][nelx+1][2];
  * loads on clamped DOFs are ignored.  u_dev: device, same layout; in: the
  * warm start (zeros for a cold start), out: the solution, zero on clamped
- * DOFs.  stats: host, may be NULL (then the call only enqueues work and
- * returns MTO_OK; the outcome can be read with mto_last_stats).  With stats,
- * the call synchronises and returns MTO_ERR_NOT_CONVERGED or
- * MTO_ERR_BREAKDOWN when a right-hand side failed; stats describe the last
- * right-hand side (iters summed over all). */
+ * DOFs.  stats: host, may be NULL.  Returns MTO_ERR_NOT_CONVERGED or
+ * MTO_ERR_BREAKDOWN when a right-hand side failed (u then holds its last
+ * iterate); stats describe the last right-hand side, with iters summed over
+ * all of them. */
 mto_status mto_solve(mto_ctx* ctx, int n_rhs, const double* f_dev, double* u_dev,
                      mto_solve_stats* stats);
 
@@ -156,8 +157,25 @@ mto_status mto_apply_preconditioner(mto_ctx* ctx, const double* r_dev, double* z
 mto_status mto_get_info(mto_ctx* ctx, int* n_levels, int* coarsest_free_dofs);
 mto_status mto_get_moduli(mto_ctx* ctx, double* E_dev);
 
+/* Measurement hooks.
+ * mto_set_kernel_timing(ctx, 1) records CUDA events (on the context's stream,
+ * inside the solver's CUDA graph) around two hot kernels of every PCG
+ * iteration: [0] the finest-level outer sweep p = z + beta p, q = K p (float64)
+ * and [1] the first finest-level damped-Jacobi sweep of the V-cycle (in the
+ * V-cycle's precision).  mto_get_kernel_times returns their mean duration in
+ * ms over the iterations sampled since timing was enabled (host arrays of 2).
+ * mto_get_launch_count returns the number of kernels this context has
+ * launched (each graph launch counts its kernel nodes).  Timing adds event
+ * nodes to the graph; leave it off outside measurements. */
+mto_status mto_set_kernel_timing(mto_ctx* ctx, int enable);
+mto_status mto_get_kernel_times(mto_ctx* ctx, double* ms_avg, long long* samples);
+mto_status mto_get_launch_count(mto_ctx* ctx, long long* launches);
+
 void mto_destroy(mto_ctx* ctx);
 const char* mto_status_string(mto_status s);
+/* Text of the CUDA error behind the last MTO_ERR_CUDA returned to this host
+ * thread ("no error" if none). */
+const char* mto_cuda_error_string(void);
 
 #ifdef __cplusplus
 }

@@ -126,7 +126,7 @@ class Mesh:
             code = self._lib.mto_solve(self._h, n_rhs, _ptr(f), _ptr(u), ctypes.byref(st))
         if code not in (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_BREAKDOWN) or (
                 raise_on_failure and code != _lib.OK):
-            raise MtoError(code, "mto_solve")
+            _lib.check(code, "mto_solve")
         d = st.as_dict()
         d["status"] = _lib.STATUS[code]
         return u, d

@@ -84,8 +84,12 @@ SIGNATURES = {
     "mto_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
     "mto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "mto_get_moduli": (ctypes.c_int, [_P, _P]),
+    "mto_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "mto_get_kernel_times": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
+    "mto_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_destroy": (None, [_P]),
     "mto_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mto_cuda_error_string": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -111,6 +115,8 @@ def load():
 
 def check(code, where):
     if code != OK:
+        if code == ERR_CUDA and _lib is not None:
+            where = f"{where} ({_lib.mto_cuda_error_string().decode()})"
         raise MtoError(code, where)
 
 

@@ -69,6 +69,15 @@ struct mto_ctx {
   int hc_cap = 0;
   // graph of two PCG iterations
   cudaGraphExec_t gexec = nullptr;
+  long long graph_kernels = 0;  // kernel nodes in the graph
+  long long launches = 0;       // kernels launched by this context (graph nodes included)
+  // optional event pairs around the hot kernels of each graph iteration:
+  // [parity][0 = outer K p sweep, 1 = first finest-level smoothing sweep][start, end]
+  bool timing = false;
+  cudaEvent_t kev[2][2][2] = {};
+  double ksum[2] = {0.0, 0.0};
+  long long kcnt[2] = {0, 0};
+  int cur_par = -1;
   // constants
   FineConst<double> kf64{};
   FineConst<float> kf32{};
@@ -81,10 +90,23 @@ struct mto_ctx {
 
 namespace {
 
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return MTO_ERR_CUDA;    \
+// Last CUDA error that made a call of this thread return MTO_ERR_CUDA.
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+#define CK(call)                    \
+  do {                              \
+    cudaError_t e_ = (call);        \
+    if (e_ != cudaSuccess) {        \
+      g_last_cuda = e_;             \
+      return MTO_ERR_CUDA;          \
+    }                               \
+  } while (0)
+
+// A kernel launch made by the context: counted, then checked.
+#define KL(call)              \
+  do {                        \
+    c->launches += 1;         \
+    CK(call);                 \
   } while (0)
 
 #define ST(call)                          \
@@ -154,7 +176,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   const int tw = target_warps(c);
   const int nb = vec_blocks(L.g.size(), c->num_sms);
   // First pre-smoothing sweep from U = 0: U = w D^-1 F.
-  CK(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb, c->stream));
+  KL(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb, c->stream));
   int cur = 0;
   auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc) -> cudaError_t {
     SweepParams<T> p = base_params<T>(c, L.g);
@@ -171,21 +193,21 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     return launch_sweep<T>(SRC_COARSE, mode, false, false, p, sweep_shape(L.g, mode, tw), c->stream);
   };
   for (int s = 1; s < c->o.nu1; ++s) {
-    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
+    KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
     cur ^= 1;
   }
-  CK(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
+  KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
   int cidx = 0;
   if (l - 1 == 0) {
-    CK(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
+    KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
                                (T2*)C.z[0], sc, c->stream));
   } else {
     ST(coarse_cycle<T>(c, l - 1, sc, &cidx));
   }
-  CK(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));
+  KL(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));
   cur ^= 1;
   for (int s = 1; s < c->o.nu2; ++s) {
-    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
+    KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
     cur ^= 1;
   }
   *final_idx = cur;
@@ -206,11 +228,11 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   const int src = MIX ? SRC_FINEBF : SRC_FINE64;
   const T2* b;
   if constexpr (MIX) {
-    CK(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r, c->r32, (float2*)L.z[0], sc,
+    KL(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r, c->r32, (float2*)L.z[0], sc,
                              nb, c->stream));
     b = (const T2*)c->r32;
   } else {
-    CK(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->stream));
+    KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->stream));
     b = (const T2*)c->r;
   }
   int cur = 0;
@@ -235,23 +257,28 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
     }
     return launch_sweep<T>(src, mode, dot, false, p, sweep_shape(L.g, mode, tw), c->stream);
   };
+  const bool tm = c->timing && sc != nullptr && c->cur_par >= 0;
   for (int s = 1; s < c->o.nu1; ++s) {
-    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr, false));
+    if (tm && s == 1)
+      CK(cudaEventRecordWithFlags(c->kev[c->cur_par][1][0], c->stream, cudaEventRecordExternal));
+    KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr, false));
+    if (tm && s == 1)
+      CK(cudaEventRecordWithFlags(c->kev[c->cur_par][1][1], c->stream, cudaEventRecordExternal));
     cur ^= 1;
   }
-  CK(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr, false));
+  KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr, false));
   int cidx = 0;
   if (c->L - 1 == 0) {
-    CK(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
+    KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
                                (T2*)C.z[0], sc, c->stream));
   } else {
     ST(coarse_cycle<T>(c, c->L - 1, sc, &cidx));
   }
-  CK(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx],
+  KL(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx],
            with_dot && c->o.nu2 == 1));
   cur ^= 1;
   for (int s = 1; s < c->o.nu2; ++s) {
-    CK(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr,
+    KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr,
              with_dot && s == c->o.nu2 - 1));
     cur ^= 1;
   }
@@ -273,7 +300,7 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.E = c->E64;
   p.kf = c->kf64;
   p.finish = finish;
-  CK(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
+  KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
                           sweep_shape(g, MODE_RESID, target_warps(c)), c->stream));
   return MTO_OK;
 }
@@ -281,6 +308,7 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
 // One PCG iteration (Alg. 2) with search directions p[par] -> p[par ^ 1].
 mto_status enqueue_iteration(mto_ctx* c, int par) {
   const Grid& g = c->lv[c->L].g;
+  c->cur_par = par;
   int zi = 0;
   const void* z;
   if (c->mixed) {
@@ -289,6 +317,9 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     ST(fine_cycle<double>(c, c->sc, true, &zi));
   }
   z = c->lv[c->L].z[zi];
+  // External event-record nodes inside the captured graph (a plain record
+  // during capture would only mark a dependency).
+  if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][0], c->stream, cudaEventRecordExternal));
   {
     SweepParams<double> p = base_params<double>(c, g);
     p.gate = 1;
@@ -300,10 +331,11 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.E = c->E64;
     p.kf = c->kf64;
     p.finish = FIN_PQ;
-    CK(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
+    KL(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
                             sweep_shape(g, MODE_KP, target_warps(c)), c->stream));
   }
-  CK(launch_update(g, c->x, c->r, c->p[par ^ 1], c->q, c->partials, c->ticket, c->sc,
+  if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->stream, cudaEventRecordExternal));
+  KL(launch_update(g, c->x, c->r, c->p[par ^ 1], c->q, c->partials, c->ticket, c->sc,
                    vec_blocks(g.size(), c->num_sms), c->stream));
   if (c->mixed && c->o.rr_every > 0) ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1));
   return MTO_OK;
@@ -313,9 +345,13 @@ mto_status build_graph(mto_ctx* c) {
   if (c->gexec) return MTO_OK;
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = c->launches;
   mto_status s0 = enqueue_iteration(c, 0);
   mto_status s1 = s0 == MTO_OK ? enqueue_iteration(c, 1) : s0;
+  c->cur_par = -1;
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  c->graph_kernels = c->launches - before;
+  c->launches = before;
   if (s1 != MTO_OK) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
@@ -341,8 +377,8 @@ bool valid_opts(const mto_solver_opts& o) {
 
 mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_out) {
   const Grid& g = c->lv[c->L].g;
-  CK(launch_pack(g, f_dev, c->f, c->stream, c->num_sms));
-  CK(launch_pack(g, u_dev, c->x, c->stream, c->num_sms));
+  KL(launch_pack(g, f_dev, c->f, c->stream, c->num_sms));
+  KL(launch_pack(g, u_dev, c->x, c->stream, c->num_sms));
   DevScalars s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.tol2 = c->o.tol * c->o.tol;
@@ -352,7 +388,7 @@ mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_
   *c->sc_host = s0;
   CK(cudaMemcpyAsync(c->sc, c->sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->p[0], 0, sizeof(double2) * g.size(), c->stream));
-  CK(launch_dot(g.size(), c->f, c->f, c->partials, c->ticket, c->sc, FIN_FF, nullptr,
+  KL(launch_dot(g.size(), c->f, c->f, c->partials, c->ticket, c->sc, FIN_FF, nullptr,
                 vec_blocks(g.size(), c->num_sms), c->stream));
   ST(fine_resid(c, c->x, c->f, c->r, FIN_INIT_RR, 0, 0));
   ST(build_graph(c));
@@ -361,14 +397,28 @@ mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_
   for (;;) {
     CK(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->timing && launched > 0 && c->sc_host->done == RUNNING) {
+      // Every iteration of the last graph launch ran in full: sample it.
+      for (int par = 0; par < 2; ++par)
+        for (int k = 0; k < 2; ++k) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, c->kev[par][k][0], c->kev[par][k][1]) == cudaSuccess) {
+            c->ksum[k] += ms;
+            c->kcnt[k] += 1;
+          } else {
+            cudaGetLastError();  // a missing sample is not a failure of the solve
+          }
+        }
+    }
     if (c->sc_host->done != RUNNING || launched > c->o.max_it + 2) break;
     for (int k = 0; k < poll; ++k) {
       CK(cudaGraphLaunch(c->gexec, c->stream));
+      c->launches += c->graph_kernels;
       launched += 2;
     }
   }
   ST(fine_resid(c, c->x, c->f, c->tmp, FIN_TRUE, 0, 0));
-  CK(launch_unpack(g, c->x, u_dev, c->stream, c->num_sms));
+  KL(launch_unpack(g, c->x, u_dev, c->stream, c->num_sms));
   CK(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   const DevScalars& h = *c->sc_host;
@@ -406,6 +456,8 @@ void mto_default_opts(mto_solver_opts* o) {
   o->check_every = 4;
 }
 
+const char* mto_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }
+
 const char* mto_status_string(mto_status s) {
   switch (s) {
     case MTO_OK: return "ok";
@@ -429,6 +481,10 @@ void mto_destroy(mto_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->err_host) cudaFreeHost(c->err_host);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int d = 0; d < 2; ++d)
+        if (c->kev[a][b][d]) cudaEventDestroy(c->kev[a][b][d]);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
@@ -592,37 +648,37 @@ static mto_status set_design_impl(mto_ctx* c, int n_phase, const double* x_dev,
   CK(cudaEventRecord(c->ev_a, c->stream));
   CK(cudaMemcpyAsync(c->xdes, x_dev, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice,
                      c->stream));
-  CK(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->stream,
+  KL(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->stream,
                     c->num_sms));
-  if (!c->mixed) CK(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->stream, c->num_sms));
+  if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->stream, c->num_sms));
   const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
   for (int l = c->L - 1; l >= 0; --l) {
     LevelBuf& B = c->lv[l];
     if (l == c->L - 1) {
-      CK(launch_moments_from_fine(B.g, gf, c->mixed ? nullptr : c->E64, c->mixed ? c->Ebf : nullptr,
+      KL(launch_moments_from_fine(B.g, gf, c->mixed ? nullptr : c->E64, c->mixed ? c->Ebf : nullptr,
                                   redisc, B.mom, c->stream, c->num_sms));
     } else {
-      CK(launch_moments_from_coarse(B.g, c->lv[l + 1].g, c->lv[l + 1].mom, redisc, B.mom, c->stream,
+      KL(launch_moments_from_coarse(B.g, c->lv[l + 1].g, c->lv[l + 1].mom, redisc, B.mom, c->stream,
                                     c->num_sms));
     }
     if (c->mixed) {
-      CK(launch_coefs<float>(B.g, B.mom, c->nu, (float*)B.coef, c->stream, c->num_sms));
+      KL(launch_coefs<float>(B.g, B.mom, c->nu, (float*)B.coef, c->stream, c->num_sms));
       if (l > 0)
-        CK(launch_coarse_invd<float>(B.g, (const float*)B.coef, c->o.omega, (float2*)B.invd2,
+        KL(launch_coarse_invd<float>(B.g, (const float*)B.coef, c->o.omega, (float2*)B.invd2,
                                      c->stream, c->num_sms));
     } else {
-      CK(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->stream, c->num_sms));
+      KL(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->stream, c->num_sms));
       if (l > 0)
-        CK(launch_coarse_invd<double>(B.g, (const double*)B.coef, c->o.omega, (double2*)B.invd2,
+        KL(launch_coarse_invd<double>(B.g, (const double*)B.coef, c->o.omega, (double2*)B.invd2,
                                       c->stream, c->num_sms));
     }
   }
   LevelBuf& B0 = c->lv[0];
-  CK(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->stream, c->num_sms));
+  KL(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->stream, c->num_sms));
   CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * c->n0, c->stream));
   CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
-  CK(launch_dense_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->Kd, c->stream));
-  CK(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->Kinv, c->err_flag, c->stream, c->num_sms));
+  KL(launch_dense_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->Kd, c->stream));
+  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->Kinv, c->err_flag, c->stream, c->num_sms));
   CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaEventRecord(c->ev_b, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -693,10 +749,10 @@ mto_status mto_compliance_grad(mto_ctx* c, int n_rhs, const double* f_dev, const
   for (int k = 0; k < n_rhs; ++k) {
     const double2* fk = reinterpret_cast<const double2*>(f_dev + 2 * nn * k);
     const double2* uk = reinterpret_cast<const double2*>(u_dev + 2 * nn * k);
-    CK(launch_dot(nn, fk, uk, c->partials, c->ticket, nullptr, FIN_NONE, compliance_dev + k,
+    KL(launch_dot(nn, fk, uk, c->partials, c->ticket, nullptr, FIN_NONE, compliance_dev + k,
                   vec_blocks(nn, c->num_sms), c->stream));
     if (dcdx_dev)
-      CK(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
+      KL(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
                             c->kf64, u_dev + 2 * nn * k, dcdx_dev, k > 0, c->stream, c->num_sms));
   }
   return leave(c);
@@ -755,35 +811,35 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
   const int tw = target_warps(c);
   const bool fine = level == c->L;
   if (fine && (!c->mixed || !use_vcycle_operator)) {
-    CK(launch_pack(B.g, v_dev, c->tmp, c->stream, c->num_sms));
+    KL(launch_pack(B.g, v_dev, c->tmp, c->stream, c->num_sms));
     SweepParams<double> p = base_params<double>(c, B.g);
     p.v = c->tmp;
     p.out = c->q;
     p.E = c->E64;
     p.kf = c->kf64;
-    CK(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
+    KL(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
                             sweep_shape(B.g, MODE_APPLY, tw), c->stream));
-    CK(launch_unpack(B.g, c->q, y_dev, c->stream, c->num_sms));
+    KL(launch_unpack(B.g, c->q, y_dev, c->stream, c->num_sms));
   } else if (c->mixed) {
-    CK(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->stream, c->num_sms));
+    KL(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->stream, c->num_sms));
     SweepParams<float> p = base_params<float>(c, B.g);
     p.v = (const float2*)B.z[0];
     p.out = (float2*)B.z[1];
     p.E = c->Ebf;
     p.kf = c->kf32;
     p.coef = (const float*)B.coef;
-    CK(launch_sweep<float>(fine ? SRC_FINEBF : SRC_COARSE, MODE_APPLY, false, false, p,
+    KL(launch_sweep<float>(fine ? SRC_FINEBF : SRC_COARSE, MODE_APPLY, false, false, p,
                            sweep_shape(B.g, MODE_APPLY, tw), c->stream));
-    CK(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->stream, c->num_sms));
+    KL(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->stream, c->num_sms));
   } else {
-    CK(launch_pack(B.g, v_dev, (double2*)B.z[0], c->stream, c->num_sms));
+    KL(launch_pack(B.g, v_dev, (double2*)B.z[0], c->stream, c->num_sms));
     SweepParams<double> p = base_params<double>(c, B.g);
     p.v = (const double2*)B.z[0];
     p.out = (double2*)B.z[1];
     p.coef = (const double*)B.coef;
-    CK(launch_sweep<double>(SRC_COARSE, MODE_APPLY, false, false, p,
+    KL(launch_sweep<double>(SRC_COARSE, MODE_APPLY, false, false, p,
                             sweep_shape(B.g, MODE_APPLY, tw), c->stream));
-    CK(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->stream, c->num_sms));
+    KL(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->stream, c->num_sms));
   }
   return leave(c);
 }
@@ -793,14 +849,14 @@ mto_status mto_apply_preconditioner(mto_ctx* c, const double* r_dev, double* z_d
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   LevelBuf& B = c->lv[c->L];
-  CK(launch_pack(B.g, r_dev, c->r, c->stream, c->num_sms));
+  KL(launch_pack(B.g, r_dev, c->r, c->stream, c->num_sms));
   int zi = 0;
   if (c->mixed) {
     ST(fine_cycle<float>(c, nullptr, false, &zi));
-    CK(launch_unpack_f32(B.g, (const float2*)B.z[zi], z_dev, c->stream, c->num_sms));
+    KL(launch_unpack_f32(B.g, (const float2*)B.z[zi], z_dev, c->stream, c->num_sms));
   } else {
     ST(fine_cycle<double>(c, nullptr, false, &zi));
-    CK(launch_unpack(B.g, (const double2*)B.z[zi], z_dev, c->stream, c->num_sms));
+    KL(launch_unpack(B.g, (const double2*)B.z[zi], z_dev, c->stream, c->num_sms));
   }
   return leave(c);
 }
@@ -816,8 +872,41 @@ mto_status mto_get_moduli(mto_ctx* c, double* E_dev) {
   if (!c || !E_dev) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
-  CK(launch_unpack_elems(c->lv[c->L].g, c->E64, E_dev, c->stream, c->num_sms));
+  KL(launch_unpack_elems(c->lv[c->L].g, c->E64, E_dev, c->stream, c->num_sms));
   return leave(c);
+}
+
+mto_status mto_set_kernel_timing(mto_ctx* c, int enable) {
+  if (!c) return MTO_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  if (enable && !c->kev[0][0][0])
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int d = 0; d < 2; ++d) CK(cudaEventCreate(&c->kev[a][b][d]));
+  if ((bool)enable != c->timing && c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->timing = enable != 0;
+  c->ksum[0] = c->ksum[1] = 0.0;
+  c->kcnt[0] = c->kcnt[1] = 0;
+  return MTO_OK;
+}
+
+mto_status mto_get_kernel_times(mto_ctx* c, double* ms_avg, long long* samples) {
+  if (!c || !ms_avg || !samples) return MTO_ERR_ARG;
+  for (int k = 0; k < 2; ++k) {
+    samples[k] = c->kcnt[k];
+    ms_avg[k] = c->kcnt[k] ? c->ksum[k] / (double)c->kcnt[k] : 0.0;
+  }
+  return MTO_OK;
+}
+
+mto_status mto_get_launch_count(mto_ctx* c, long long* launches) {
+  if (!c || !launches) return MTO_ERR_ARG;
+  *launches = c->launches;
+  return MTO_OK;
 }
 
 }  // extern "C"
