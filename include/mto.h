@@ -157,6 +157,34 @@ mto_status mto_apply_preconditioner(mto_ctx* ctx, const double* r_dev, double* z
 mto_status mto_get_info(mto_ctx* ctx, int* n_levels, int* coarsest_free_dofs);
 mto_status mto_get_moduli(mto_ctx* ctx, double* E_dev);
 
+/* Compliance and sensitivities with no device allocation and no context.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory -- code running while its stream is being captured into a
+ * CUDA graph (cudaMalloc is not allowed during capture), hosts whose memory
+ * pool owns the device's memory and forbids other allocations, and
+ * latency-critical loops that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  Computes, for one load case on an nelx x nely mesh,
+ * compliance_dev[0] = f . u and (if dcdx_dev != NULL) dcdx_dev[i][e] =
+ * -penal x_{e,i}^(penal-1) E_phase[i] u_e^T KE u_e, the same values as
+ * mto_compliance_grad (up to summation order for the compliance).
+ * Arrays: f_dev, u_dev device float64 [nely+1][nelx+1][2]; x_dev device
+ * float64 [n_phase][nely][nelx] (needed only with dcdx_dev); compliance_dev
+ * device float64 [1]; dcdx_dev device float64 [n_phase][nely][nelx];
+ * E_phase host [n_phase].  Work is enqueued on cuda_stream of `device`.
+ * Scratch: a fixed 512 KiB device array inside the library, held on every GPU
+ * that loads it until the process exits; meshes above 33,554,432 nodes are
+ * rejected with MTO_ERR_UNSUPPORTED_MESH.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array and clears its counter at the start; calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
+mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu, int n_phase,
+                                       const double* x_dev, const double* E_phase, double penal,
+                                       const double* f_dev, const double* u_dev,
+                                       double* compliance_dev, double* dcdx_dev, int device,
+                                       void* cuda_stream);
+
 /* Measurement hooks.
  * mto_set_kernel_timing(ctx, 1) records CUDA events (on the context's stream,
  * inside the solver's CUDA graph) around two hot kernels of every PCG

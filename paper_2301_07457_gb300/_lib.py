@@ -84,6 +84,9 @@ SIGNATURES = {
     "mto_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
     "mto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "mto_get_moduli": (ctypes.c_int, [_P, _P]),
+    "mto_compliance_grad_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                   _P, _D, ctypes.c_double, _P, _P, _P, _P, ctypes.c_int,
+                                                   _P]),
     "mto_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "mto_get_kernel_times": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
