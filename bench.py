@@ -28,14 +28,14 @@ EP = [1.0, 0.5, 0.25, 1e-9]
 PENAL = 3.0
 SEED = 0
 # Algorithmic work per finest-level node of the two timed kernels:
-#  * outer sweep p = z + beta p, q = K p, p.q in float64: 48 FP64 pipe
-#    operations (15 strain-coordinate add/sub, 11 core mul/fma, 12 force add/sub,
-#    6 node-assembly adds, 2 fma for p, 2 fma for the dot);
+#  * outer sweep p = z + beta p, q = K p, p.q in float64: 36 FP64 pipe
+#    operations (11 edge-difference add/sub, 7 core mul/fma on pre-scaled
+#    moduli, 14 edge-force add/sub, 2 fma for p, 2 fma for the dot);
 #  * float32 damped-Jacobi sweep: reads z (8 B) and b (8 B), the element's
 #    bf16 modulus (2 B), writes z (8 B): 26 B.
-KP_OPS_PER_NODE = 48
+KP_OPS_PER_NODE = 36
 SMOOTH32_BYTES_PER_NODE = 26
-SMOOTH64_OPS_PER_NODE = 48
+SMOOTH64_OPS_PER_NODE = 38  # K v 32, w D^-1 b 2, z + d (b - K v) 4 (first two sweeps fused)
 # FP64 pipe: 2 operations per clock per SM (1.25 TFLOP/s nominal at 2 flops
 # per FMA), 152 SMs, 2070 MHz.
 FP64_OPS_PEAK = 2 * 152 * 2.070e9
@@ -69,14 +69,17 @@ def peaks():
 # Clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi samples (every 50 ms) kept only inside the timed window."""
+
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}_{index}.csv")
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -84,13 +87,17 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let the sampler start before the timed region
         except Exception:
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *a):
+        self.t1 = time.time()
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -99,22 +106,35 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
         with open(self.path) as fh:
             for line in fh:
                 p = [t.strip() for t in line.split(",")]
-                if len(p) >= 7:
-                    rows.append(p)
-        if not rows:
+                if len(p) < 8:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                rows.append((ts, p[1:]))
+        inside = [r for ts, r in rows if self.t0 - 0.05 <= ts <= self.t1 + 0.05] or [r for _, r in rows]
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = sorted(float(r[0]) for r in rows if r[0].replace(".", "").isdigit())
-        smax = max(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(r[0]) for r in inside) if v is not None)
+        smax = max((v for v in (num(r[1]) for r in inside) if v is not None), default=None)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[3 + k].lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(inside)}
 
 
 # ---------------------------------------------------------------------------

@@ -39,6 +39,7 @@ struct mto_ctx {
   std::vector<LevelBuf> lv;
   // finest level
   double* E64 = nullptr;
+  double* Ek4 = nullptr;  // E (kA, kB, kC, kG) per element, for the float64 sweeps
   __nv_bfloat16* Ebf = nullptr;
   double* invd1 = nullptr;
   double2 *x = nullptr, *r = nullptr, *q = nullptr, *f = nullptr, *tmp = nullptr;
@@ -175,8 +176,6 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   LevelBuf& C = c->lv[l - 1];
   const int tw = target_warps(c);
   const int nb = vec_blocks(L.g.size(), c->num_sms);
-  // First pre-smoothing sweep from U = 0: U = w D^-1 F.
-  KL(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb, c->stream));
   int cur = 0;
   auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc) -> cudaError_t {
     SweepParams<T> p = base_params<T>(c, L.g);
@@ -192,7 +191,15 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     p.invd2 = (const T2*)L.invd2;
     return launch_sweep<T>(SRC_COARSE, mode, false, false, p, sweep_shape(L.g, mode, tw), c->stream);
   };
-  for (int s = 1; s < c->o.nu1; ++s) {
+  // Pre-smoothing from U = 0: the first sweep (U = w D^-1 F) is formed on the
+  // fly inside the second when there are two or more.
+  if (c->o.nu1 >= 2) {
+    KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr));
+  } else {
+    KL(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb,
+                                c->stream));
+  }
+  for (int s = 2; s < c->o.nu1; ++s) {
     KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
     cur ^= 1;
   }
@@ -227,12 +234,15 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   const int nb = vec_blocks(L.g.size(), c->num_sms);
   const int src = MIX ? SRC_FINEBF : SRC_FINE64;
   const T2* b;
+  // float64: the first pre-sweep from zero is fused into the second (SMOOTH0).
+  // mixed: the pointwise first sweep also writes the float32 copy of r.
+  const bool fused0 = !MIX && c->o.nu1 >= 2;
   if constexpr (MIX) {
     KL(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r, c->r32, (float2*)L.z[0], sc,
                              nb, c->stream));
     b = (const T2*)c->r32;
   } else {
-    KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->stream));
+    if (!fused0) KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->stream));
     b = (const T2*)c->r;
   }
   int cur = 0;
@@ -246,7 +256,7 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
     p.b = b;
     p.out = out;
     p.bc = (T2*)C.b;
-    p.E = MIX ? (const void*)c->Ebf : (const void*)c->E64;
+    p.E = MIX ? (const void*)c->Ebf : (const void*)c->Ek4;
     p.kf = fine_const<T>(c);
     p.invd1 = c->invd1;
     p.wdiag = T(c->w_over_kdiag);
@@ -257,13 +267,27 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
     }
     return launch_sweep<T>(src, mode, dot, false, p, sweep_shape(L.g, mode, tw), c->stream);
   };
+  // Timing events bracket the first finest-level smoothing kernel.
   const bool tm = c->timing && sc != nullptr && c->cur_par >= 0;
-  for (int s = 1; s < c->o.nu1; ++s) {
-    if (tm && s == 1)
-      CK(cudaEventRecordWithFlags(c->kev[c->cur_par][1][0], c->stream, cudaEventRecordExternal));
+  auto t0 = [&]() -> cudaError_t {
+    return tm ? cudaEventRecordWithFlags(c->kev[c->cur_par][1][0], c->stream, cudaEventRecordExternal)
+              : cudaSuccess;
+  };
+  auto t1 = [&]() -> cudaError_t {
+    return tm ? cudaEventRecordWithFlags(c->kev[c->cur_par][1][1], c->stream, cudaEventRecordExternal)
+              : cudaSuccess;
+  };
+  int first = 1;
+  if (fused0) {
+    CK(t0());
+    KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr, false));
+    CK(t1());
+    first = 2;
+  }
+  for (int s = first; s < c->o.nu1; ++s) {
+    if (s == 1) CK(t0());
     KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr, false));
-    if (tm && s == 1)
-      CK(cudaEventRecordWithFlags(c->kev[c->cur_par][1][1], c->stream, cudaEventRecordExternal));
+    if (s == 1) CK(t1());
     cur ^= 1;
   }
   KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr, false));
@@ -297,8 +321,7 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.v = v;
   p.b = b;
   p.out = out;
-  p.E = c->E64;
-  p.kf = c->kf64;
+  p.E = c->Ek4;
   p.finish = finish;
   KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
                           sweep_shape(g, MODE_RESID, target_warps(c)), c->stream));
@@ -328,8 +351,7 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.zkp = z;
     p.p_out = c->p[par ^ 1];
     p.out = c->q;
-    p.E = c->E64;
-    p.kf = c->kf64;
+    p.E = c->Ek4;
     p.finish = FIN_PQ;
     KL(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
                             sweep_shape(g, MODE_KP, target_warps(c)), c->stream));
@@ -544,6 +566,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   const Grid& gf = c->lv[c->L].g;
   const size_t nf = (size_t)gf.size();
   ST(dalloc_t(c, &c->E64, nf));
+  ST(dalloc_t(c, &c->Ek4, 4 * nf));
   if (c->mixed) {
     ST(dalloc_t(c, &c->Ebf, nf));
     ST(dalloc_t(c, &c->r32, nf));
@@ -648,8 +671,8 @@ static mto_status set_design_impl(mto_ctx* c, int n_phase, const double* x_dev,
   CK(cudaEventRecord(c->ev_a, c->stream));
   CK(cudaMemcpyAsync(c->xdes, x_dev, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice,
                      c->stream));
-  KL(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->stream,
-                    c->num_sms));
+  KL(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->Ek4, c->kf64,
+                    c->stream, c->num_sms));
   if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->stream, c->num_sms));
   const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
   for (int l = c->L - 1; l >= 0; --l) {
@@ -815,8 +838,7 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     SweepParams<double> p = base_params<double>(c, B.g);
     p.v = c->tmp;
     p.out = c->q;
-    p.E = c->E64;
-    p.kf = c->kf64;
+    p.E = c->Ek4;
     KL(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
                             sweep_shape(B.g, MODE_APPLY, tw), c->stream));
     KL(launch_unpack(B.g, c->q, y_dev, c->stream, c->num_sms));

@@ -58,8 +58,10 @@ struct PhaseTable {
   double E[16];
 };
 // E_e = sum_i x_{e,i}^penal E_i (Eq. 5); ipenal >= 0 selects repeated products.
+// Also writes E (kA, kB, kC, kG) per element (Ek4, 4 doubles) for the float64 sweeps.
 cudaError_t launch_modulus(const Grid& g, int n_phase, const double* x, PhaseTable ph, double penal,
-                           int ipenal, double* E64, __nv_bfloat16* Ebf, cudaStream_t s, int num_sms);
+                           int ipenal, double* E64, __nv_bfloat16* Ebf, double* Ek4,
+                           FineConst<double> kf, cudaStream_t s, int num_sms);
 // w / D on the float64 finest level (D = KE_00 * sum of the four moduli).
 cudaError_t launch_fine_invd(const Grid& g, const double* E64, double w_over_kdiag, double* invd1,
                              cudaStream_t s, int num_sms);

@@ -23,7 +23,8 @@ __device__ __forceinline__ double xpow(double x, double p, int ip) {
 
 __global__ void modulus_kernel(Grid g, int n_phase, const double* __restrict__ x, PhaseTable ph,
                                double penal, int ipenal, double* __restrict__ E64,
-                               __nv_bfloat16* __restrict__ Ebf) {
+                               __nv_bfloat16* __restrict__ Ebf, double* __restrict__ Ek4,
+                               FineConst<double> kf) {
   const long long n = (long long)g.nx * g.ny;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -33,6 +34,11 @@ __global__ void modulus_kernel(Grid g, int n_phase, const double* __restrict__ x
     const long long k = g.at(i, j);
     E64[k] = E;
     if (Ebf) Ebf[k] = __double2bfloat16(E);
+    // The fine element core's four scale factors, stored so that the float64
+    // sweeps spend no FP64 multiplies on them.
+    double2* q = reinterpret_cast<double2*>(Ek4) + 2 * k;
+    q[0] = make_double2(E * kf.kA, E * kf.kB);
+    q[1] = make_double2(E * kf.kC, E * kf.kG);
   }
 }
 
@@ -338,9 +344,10 @@ static int blocks_for(long long n, int num_sms) {
 }
 
 cudaError_t launch_modulus(const Grid& g, int n_phase, const double* x, PhaseTable ph, double penal,
-                           int ipenal, double* E64, __nv_bfloat16* Ebf, cudaStream_t s, int num_sms) {
+                           int ipenal, double* E64, __nv_bfloat16* Ebf, double* Ek4,
+                           FineConst<double> kf, cudaStream_t s, int num_sms) {
   modulus_kernel<<<blocks_for((long long)g.nx * g.ny, num_sms), 256, 0, s>>>(g, n_phase, x, ph, penal,
-                                                                             ipenal, E64, Ebf);
+                                                                             ipenal, E64, Ebf, Ek4, kf);
   return cudaGetLastError();
 }
 

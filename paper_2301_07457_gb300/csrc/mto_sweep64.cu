@@ -1,5 +1,6 @@
 // float64 instantiations of the marching sweeps (finest level with float64
-// moduli, coarse levels with float64 element matrices).
+// moduli, coarse levels with float64 element matrices).  These kernels are
+// bound by the FP64 pipe, so one step of load lookahead suffices.
 #include "mto_launch.h"
 
 namespace mto {
@@ -8,14 +9,14 @@ SweepShape sweep_shape(const Grid& g, int mode, int target_warps) {
   SweepShape sh;
   if (mode == MODE_RESTRICT) {
     const int nxc = g.nx / 2, nyc = g.ny / 2;
-    sh.nstrips = (nxc + 1 + 14) / 15;
+    sh.nstrips = (nxc + 1 + SWEEP_RSTRIDE / 2 - 1) / (SWEEP_RSTRIDE / 2);
     const int want = target_warps / sh.nstrips > 1 ? target_warps / sh.nstrips : 1;
     int hc = (nyc + 1 + want - 1) / want;
     hc = hc < 1 ? 1 : (hc > 32 ? 32 : hc);
     sh.H = 2 * hc;
     sh.nchunks = (nyc + 1 + hc - 1) / hc;
   } else {
-    sh.nstrips = (g.nx + 1 + 30) / 31;
+    sh.nstrips = (g.nx + 1 + SWEEP_STRIDE - 1) / SWEEP_STRIDE;
     const int want = target_warps / sh.nstrips > 1 ? target_warps / sh.nstrips : 1;
     int h = (g.ny + 1 + want - 1) / want;
     h = h < 2 ? 2 : (h > 64 ? 64 : h);
@@ -29,7 +30,7 @@ SweepShape sweep_shape(const Grid& g, int mode, int target_warps) {
 
 template <int SRC, int MODE, bool DOT, typename ZT>
 static cudaError_t go(const SweepParams<double>& p, const SweepShape& sh, cudaStream_t s) {
-  sweep_kernel<double, SRC, MODE, DOT, ZT><<<sh.nblocks, SWEEP_NT, 0, s>>>(p);
+  sweep_kernel<double, SRC, MODE, DOT, ZT, 1><<<sh.nblocks, SWEEP_NT, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -49,6 +50,7 @@ cudaError_t launch_sweep<double>(int src, int mode, bool dot, bool zfloat, Sweep
       case MODE_SMOOTH:
         return dot ? go<SRC_FINE64, MODE_SMOOTH, true, double2>(p, sh, s)
                    : go<SRC_FINE64, MODE_SMOOTH, false, double2>(p, sh, s);
+      case MODE_SMOOTH0: return go<SRC_FINE64, MODE_SMOOTH0, false, double2>(p, sh, s);
       case MODE_PSMOOTH:
         return dot ? go<SRC_FINE64, MODE_PSMOOTH, true, double2>(p, sh, s)
                    : go<SRC_FINE64, MODE_PSMOOTH, false, double2>(p, sh, s);
@@ -60,6 +62,7 @@ cudaError_t launch_sweep<double>(int src, int mode, bool dot, bool zfloat, Sweep
     switch (mode) {
       case MODE_APPLY: return go<SRC_COARSE, MODE_APPLY, false, double2>(p, sh, s);
       case MODE_SMOOTH: return go<SRC_COARSE, MODE_SMOOTH, false, double2>(p, sh, s);
+      case MODE_SMOOTH0: return go<SRC_COARSE, MODE_SMOOTH0, false, double2>(p, sh, s);
       case MODE_PSMOOTH: return go<SRC_COARSE, MODE_PSMOOTH, false, double2>(p, sh, s);
       case MODE_RESTRICT: return go<SRC_COARSE, MODE_RESTRICT, false, double2>(p, sh, s);
       default: return cudaErrorInvalidValue;
