@@ -48,7 +48,7 @@ struct mto_ctx {
   // coarsest grid
   int n0 = 0, bw0 = 0;
   int* dof_index = nullptr;
-  double *Kd = nullptr, *Kinv = nullptr;
+  double *Kd = nullptr, *Kinv = nullptr, *invL = nullptr;  // Kd: band storage of K_0 / its factor
   int* err_flag = nullptr;
   // reductions
   double* partials = nullptr;
@@ -164,8 +164,18 @@ template <typename T> SweepParams<T> base_params(const mto_ctx* c, const Grid& g
 }
 
 template <typename T> FineConst<T> fine_const(const mto_ctx* c);
+
+// SRC_CFINE parameters: the finest bf16 moduli and their grid.
+template <typename T> void set_cfine(const mto_ctx* c, SweepParams<T>& p);
 template <> FineConst<double> fine_const<double>(const mto_ctx* c) { return c->kf64; }
 template <> FineConst<float> fine_const<float>(const mto_ctx* c) { return c->kf32; }
+
+template <typename T> void set_cfine(const mto_ctx* c, SweepParams<T>& p) {
+  p.E = c->Ebf;
+  p.gfine = c->lv[c->L].g;
+  p.kf = fine_const<T>(c);
+  p.redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
+}
 
 // One V-cycle (Alg. 1) on coarse level l >= 1 with right-hand side lv[l].b.
 // Returns the index of the z buffer that holds the result.
@@ -177,6 +187,11 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   const int tw = target_warps(c);
   const int nb = vec_blocks(L.g.size(), c->num_sms);
   int cur = 0;
+  // The first coarse level of the mixed path rebuilds its element matrices
+  // from the bf16 fine moduli (SRC_CFINE); other coarse levels read stored
+  // coefficients.
+  const bool cfine = sizeof(T) == 4 && l == c->L - 1;
+  const int src = cfine ? SRC_CFINE : SRC_COARSE;
   auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc) -> cudaError_t {
     SweepParams<T> p = base_params<T>(c, L.g);
     p.gc = C.g;
@@ -189,7 +204,8 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     p.bc = (T2*)C.b;
     p.coef = (const T*)L.coef;
     p.invd2 = (const T2*)L.invd2;
-    return launch_sweep<T>(SRC_COARSE, mode, false, false, p, sweep_shape(L.g, mode, tw), c->stream);
+    if (cfine) set_cfine(c, p);
+    return launch_sweep<T>(src, mode, false, false, p, sweep_shape(L.g, mode, tw), c->stream);
   };
   // Pre-smoothing from U = 0: the first sweep (U = w D^-1 F) is formed on the
   // fly inside the second when there are two or more.
@@ -312,11 +328,12 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
 
 // out = b - K v on the finest level in float64 (RESID), with a finishing action.
 mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* out, int finish,
-                      int gate, int replace_gate) {
+                      int gate, int replace_gate, int zero_gate = 0) {
   const Grid& g = c->lv[c->L].g;
   SweepParams<double> p = base_params<double>(c, g);
   p.gate = gate;
   p.replace_gate = replace_gate;
+  p.zero_gate = zero_gate;
   p.sc = c->sc;
   p.v = v;
   p.b = b;
@@ -399,8 +416,6 @@ bool valid_opts(const mto_solver_opts& o) {
 
 mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_out) {
   const Grid& g = c->lv[c->L].g;
-  KL(launch_pack(g, f_dev, c->f, c->stream, c->num_sms));
-  KL(launch_pack(g, u_dev, c->x, c->stream, c->num_sms));
   DevScalars s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.tol2 = c->o.tol * c->o.tol;
@@ -409,10 +424,12 @@ mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_
   s0.rr_every = c->mixed ? c->o.rr_every : 0;
   *c->sc_host = s0;
   CK(cudaMemcpyAsync(c->sc, c->sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
+  KL(launch_pack(g, f_dev, c->f, c->stream, c->num_sms));
+  KL(launch_pack(g, u_dev, c->x, c->stream, c->num_sms, &c->sc->x_nonzero));
   CK(cudaMemsetAsync(c->p[0], 0, sizeof(double2) * g.size(), c->stream));
   KL(launch_dot(g.size(), c->f, c->f, c->partials, c->ticket, c->sc, FIN_FF, nullptr,
                 vec_blocks(g.size(), c->num_sms), c->stream));
-  ST(fine_resid(c, c->x, c->f, c->r, FIN_INIT_RR, 0, 0));
+  ST(fine_resid(c, c->x, c->f, c->r, FIN_INIT_RR, 0, 0, 1));
   ST(build_graph(c));
   const int poll = (c->o.check_every + 1) / 2;  // graph launches (2 iterations each) per poll
   int launched = 0;
@@ -616,7 +633,8 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   std::memcpy(dof.data() + 2 * (size_t)g0.size(), inv.data(), sizeof(int) * c->n0);
   ST(dalloc_t(c, &c->dof_index, dof.size()));
   CK(cudaMemcpy(c->dof_index, dof.data(), sizeof(int) * dof.size(), cudaMemcpyHostToDevice));
-  ST(dalloc_t(c, &c->Kd, (size_t)c->n0 * c->n0));
+  ST(dalloc_t(c, &c->Kd, (size_t)c->n0 * (c->bw0 + 1)));
+  ST(dalloc_t(c, &c->invL, (size_t)c->n0));
   ST(dalloc_t(c, &c->Kinv, (size_t)c->n0 * c->n0));
   ST(dalloc_t(c, &c->err_flag, 1));
 
@@ -698,10 +716,12 @@ static mto_status set_design_impl(mto_ctx* c, int n_phase, const double* x_dev,
   }
   LevelBuf& B0 = c->lv[0];
   KL(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->stream, c->num_sms));
-  CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * c->n0, c->stream));
+  CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * (c->bw0 + 1), c->stream));
   CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
-  KL(launch_dense_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->Kd, c->stream));
-  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->Kinv, c->err_flag, c->stream, c->num_sms));
+  KL(launch_band_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->bw0, c->Kd, c->stream));
+  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Kinv, c->err_flag, c->stream,
+                             c->num_sms));
+  c->launches += 1;  // the inverse is a second kernel
   CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaEventRecord(c->ev_b, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -850,8 +870,10 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     p.E = c->Ebf;
     p.kf = c->kf32;
     p.coef = (const float*)B.coef;
-    KL(launch_sweep<float>(fine ? SRC_FINEBF : SRC_COARSE, MODE_APPLY, false, false, p,
-                           sweep_shape(B.g, MODE_APPLY, tw), c->stream));
+    const bool cfine = level == c->L - 1;
+    if (cfine) set_cfine(c, p);
+    KL(launch_sweep<float>(fine ? SRC_FINEBF : (cfine ? SRC_CFINE : SRC_COARSE), MODE_APPLY, false,
+                           false, p, sweep_shape(B.g, MODE_APPLY, tw), c->stream));
     KL(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->stream, c->num_sms));
   } else {
     KL(launch_pack(B.g, v_dev, (double2*)B.z[0], c->stream, c->num_sms));

@@ -177,7 +177,8 @@ struct DevScalars {
   double tol2;      // tol^2
   double rr_true;   // ||f - K u||^2 (final check)
   double dot;       // scratch result of a plain dot kernel
-  int iter, max_it, done, flexible, rr_every, pad;
+  int iter, max_it, done, flexible, rr_every;
+  int x_nonzero;    // set by the packing of the warm start when any entry is non-zero
 };
 
 // Finishing actions of the last block of a reduction.

@@ -41,7 +41,9 @@ cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* 
                        unsigned* ticket, DevScalars* sc, int finish, double* out_value,
                        int nblocks, cudaStream_t s);
 // dense [ny+1][nx+1][2] <-> padded layout (pack zeroes clamped DOFs).
-cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms);
+// With nonzero != NULL, sets *nonzero = 1 when any packed value is non-zero.
+cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms,
+                        int* nonzero = nullptr);
 cudaError_t launch_unpack(const Grid& g, const double2* src, double* dst, cudaStream_t s, int num_sms);
 cudaError_t launch_pack_f32(const Grid& g, const double* src, float2* dst, cudaStream_t s, int num_sms);
 cudaError_t launch_unpack_f32(const Grid& g, const float2* src, double* dst, cudaStream_t s, int num_sms);
@@ -78,12 +80,13 @@ cudaError_t launch_coefs(const Grid& g, const double* mom, double nu, T* coef, c
 template <typename T>
 cudaError_t launch_coarse_invd(const Grid& g, const T* coef, double omega,
                                typename V2<T>::t* invd2, cudaStream_t s, int num_sms);
-// Dense coarsest matrix from float64 coefficients of level 0 (rows of free DOFs).
-cudaError_t launch_dense_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
-                                  double* Kd, cudaStream_t s);
-// In-place banded Cholesky of Kd (lower triangle), then the explicit inverse.
-cudaError_t launch_cholesky_inverse(int n, int bw, double* Kd, double* Kinv, int* err_flag,
-                                    cudaStream_t s, int num_sms);
+// Coarsest matrix from float64 coefficients of level 0, lower band storage
+// Kb[r * (bw + 1) + d] = K_0[r][r - d] (zeroed by the caller).
+cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
+                                 int bw, double* Kb, cudaStream_t s);
+// In-place band Cholesky of Kb (1 / L_ii to invL), then the explicit inverse.
+cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
+                                    int* err_flag, cudaStream_t s, int num_sms);
 // dcdx (+)= -penal x^(penal-1) E_i w_e, w_e = u_e^T KE u_e (dense user layouts).
 cudaError_t launch_sensitivity(int nelx, int nely, int n_phase, const double* x, PhaseTable ph,
                                double penal, int ipenal, FineConst<double> kf, const double* u,

@@ -5,8 +5,8 @@
 //     element (exact P^T K P for nested bilinear spaces) or the rediscretised
 //     mean modulus (Sec. 2.1), their 13 strain-basis coefficients and the
 //     Jacobi diagonals of every coarse level;
-//   * the coarsest grid (Alg. 1, l = 0): dense K_0 on the free DOFs, its
-//     Cholesky factor (Alg. 3) restricted to the band, and K_0^-1;
+//   * the coarsest grid (Alg. 1, l = 0): K_0 on the free DOFs in band
+//     storage, its Cholesky factor (Alg. 3), and the explicit K_0^-1;
 //   * sensitivities dC/dx_{e,i} = -p x^{p-1} E_i u_e^T KE u_e (Eq. 6, Sec. 4).
 #include "mto_launch.h"
 
@@ -185,10 +185,11 @@ __global__ void coarse_invd_kernel(Grid g, const T* __restrict__ coef, double om
   }
 }
 
-// Row r of the dense coarsest matrix: DOF (node (i, j), component c).
-__global__ void dense_assemble_kernel(Grid g, const double* __restrict__ coef,
-                                      const int* __restrict__ dof_index, int n,
-                                      double* __restrict__ Kd) {
+// Row r of the coarsest matrix K_0 (free DOF (node (i, j), component c)) in
+// lower band storage: Kb[r * (bw + 1) + d] = K_0[r][r - d], d = 0..bw.
+__global__ void band_assemble_kernel(Grid g, const double* __restrict__ coef,
+                                     const int* __restrict__ dof_index, int n, int bw,
+                                     double* __restrict__ Kb) {
   const long long s = g.size();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     // Find the node of row r: scan is avoided by storing the inverse map in
@@ -197,7 +198,7 @@ __global__ void dense_assemble_kernel(Grid g, const double* __restrict__ coef,
     const long long k = sidx >> 1;
     const int c = sidx & 1;
     const int j = (int)(k / g.pitch) - 1, i = (int)(k % g.pitch) - OFFX;
-    double* row = Kd + (long long)r * n;
+    double* row = Kb + (long long)r * (bw + 1);
     const int ei[4] = {i - 1, i, i - 1, i}, ej[4] = {j - 1, j - 1, j, j}, eq[4] = {2, 3, 1, 0};
     for (int t = 0; t < 4; ++t) {
       if (ei[t] < 0 || ei[t] >= g.nx || ej[t] < 0 || ej[t] >= g.ny) continue;
@@ -237,8 +238,8 @@ __global__ void dense_assemble_kernel(Grid g, const double* __restrict__ coef,
         const double ex = Aj[0] * t1 + Aj[1] * t3 + Aj[4] * t2;  // u_x column of node m
         const double ey = Aj[2] * t2 + Aj[3] * t3 + Aj[4] * t1;  // u_y column
         const int cx = dof_index[2 * kn], cy = dof_index[2 * kn + 1];
-        if (cx >= 0) row[cx] += ex;
-        if (cy >= 0) row[cy] += ey;
+        if (cx >= 0 && cx <= r && r - cx <= bw) row[r - cx] += ex;
+        if (cy >= 0 && cy <= r && r - cy <= bw) row[r - cy] += ey;
       }
     }
   }
@@ -246,67 +247,135 @@ __global__ void dense_assemble_kernel(Grid g, const double* __restrict__ coef,
 
 constexpr int CHOL_NT = 512;
 
-// Right-looking Cholesky (Alg. 3, textbook indices) restricted to the band
-// |i - j| <= bw of the lower triangle, one block.
-__global__ void __launch_bounds__(CHOL_NT) cholesky_band_kernel(int n, int bw, double* A, int* err) {
-  extern __shared__ short2 pairs[];  // (row, col) offsets of the trailing triangle
+// Right-looking Cholesky (Alg. 3, textbook indices) of the band matrix in
+// lower band storage B[i * (bw + 1) + d] = A[i][i - d], one block.  A band
+// matrix keeps its factor inside the band.  With SMEM the band lives in shared
+// memory for the whole factorisation.  Also writes 1 / L_ii.
+template <bool SMEM>
+__global__ void __launch_bounds__(CHOL_NT)
+    cholesky_band_kernel(int n, int bw, double* Bg, double* invL, int* err) {
+  extern __shared__ double dyn[];
   __shared__ double piv;
-  const int npmax = bw * (bw + 1) / 2;
+  const int W = bw + 1;
+  double* B = SMEM ? dyn : Bg;
+  short2* pairs = reinterpret_cast<short2*>(SMEM ? dyn + (size_t)n * W : dyn);
+  if (SMEM)
+    for (int t = threadIdx.x; t < n * W; t += CHOL_NT) B[t] = Bg[t];
   for (int ii = threadIdx.x; ii < bw; ii += CHOL_NT)
     for (int jj = 0; jj <= ii; ++jj) pairs[ii * (ii + 1) / 2 + jj] = make_short2((short)ii, (short)jj);
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
-      double d = A[(long long)k * n + k];
+      double d = B[(size_t)k * W];
       if (!(d > 0.0) || !(d < 1.0e300)) {
         *err = 1;
         d = 1.0;
       }
       d = sqrt(d);
-      A[(long long)k * n + k] = d;
-      piv = d;
+      B[(size_t)k * W] = d;
+      piv = 1.0 / d;
+      invL[k] = piv;
     }
     __syncthreads();
     const int last = min(n - 1, k + bw);
-    for (int i = k + 1 + threadIdx.x; i <= last; i += CHOL_NT) A[(long long)i * n + k] /= piv;
+    for (int i = k + 1 + threadIdx.x; i <= last; i += CHOL_NT) B[(size_t)i * W + (i - k)] *= piv;
     __syncthreads();
     const int m = last - k;
     const int np = m * (m + 1) / 2;
-    for (int t = threadIdx.x; t < np && t < npmax; t += CHOL_NT) {
+    for (int t = threadIdx.x; t < np; t += CHOL_NT) {
       const short2 pr = pairs[t];
       const int i = k + 1 + pr.x, j = k + 1 + pr.y;
-      A[(long long)i * n + j] -= A[(long long)i * n + k] * A[(long long)j * n + k];
+      B[(size_t)i * W + (i - j)] -= B[(size_t)i * W + (i - k)] * B[(size_t)j * W + (j - k)];
     }
     __syncthreads();
   }
+  if (SMEM)
+    for (int t = threadIdx.x; t < n * W; t += CHOL_NT) Bg[t] = B[t];
 }
 
-// Column j of K_0^-1 (= row j, by symmetry): L y = e_j, then L^T x = y, with
-// row j of Kinv as the workspace.  One warp per column.
-__global__ void inverse_kernel(int n, int bw, const double* __restrict__ L, double* __restrict__ Kinv) {
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= n) return;
-  double* y = Kinv + (long long)j * n;
-  for (int i = lane; i < j; i += 32) y[i] = 0.0;
-  __syncwarp();
-  for (int i = j; i < n; ++i) {
-    double s = 0.0;
-    const int k0 = max(j, i - bw);
-    for (int k = k0 + lane; k < i; k += 32) s += L[(long long)i * n + k] * y[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[i] = ((i == j ? 1.0 : 0.0) - s) / L[(long long)i * n + i];
-    __syncwarp();
+// K_0^-1 by columns: L y = e_j (forward), then L^T x = y (backward), column j
+// stored in place in Kinv (row-major; K_0^-1 is symmetric, so this is also
+// row j).  Eight threads share a column: thread t of the group takes the band
+// terms d = t, t+8, ... of every row's dot product, the group adds its
+// partial sums by shuffles, and every member then holds the new value.  Each
+// thread keeps the last bw + 1 values of its column in a shared-memory ring
+// (slot-major, so the 32 threads of a warp hit 32 distinct banks).  A warp
+// carries four columns; one warp per block, so the blocks spread over the
+// SMs, each with the factor broadcast from shared memory when it fits.
+constexpr int INV_GROUP = 8;
+constexpr int INV_COLS = 32 / INV_GROUP;
+
+template <bool LSMEM>
+__global__ void __launch_bounds__(32)
+    inverse_cols_kernel(int n, int bw, const double* __restrict__ Lg, const double* __restrict__ invL,
+                        double* __restrict__ Kinv) {
+  extern __shared__ double dyn[];
+  const int W = bw + 1;
+  const int lane = threadIdx.x;
+  const int t = lane % INV_GROUP;  // position inside the column group
+  const double* L = Lg;
+  double* win = dyn;
+  if (LSMEM) {
+    double* Ls = dyn;
+    for (int q = lane; q < n * W; q += 32) Ls[q] = Lg[q];
+    L = Ls;
+    win = dyn + (size_t)n * W;
   }
-  for (int i = n - 1; i >= 0; --i) {
-    double s = 0.0;
-    const int k1 = min(n - 1, i + bw);
-    for (int k = i + 1 + lane; k <= k1; k += 32) s += L[(long long)k * n + i] * y[k];
+  const int j0 = blockIdx.x * INV_COLS, j = j0 + lane / INV_GROUP;
+  const bool active = j < n;
+  for (int q = 0; q < W; ++q) win[q * 32 + lane] = 0.0;
+  __syncwarp();
+  // Forward substitution from row j0 (rows above j are zero for this column).
+  int slot = j0 % W;
+  for (int i = j0; i < n; ++i) {
+    double a0 = 0.0, a1 = 0.0;
+    const int dmax = min(bw, i);
+    const double* Li = L + (size_t)i * W;
+    int d = 1 + t;
+    int sd = slot - d;
+    if (sd < 0) sd += W;
+    for (; d + INV_GROUP <= dmax; d += 2 * INV_GROUP) {
+      const int sd2 = sd - INV_GROUP < 0 ? sd - INV_GROUP + W : sd - INV_GROUP;
+      a0 += Li[d] * win[sd * 32 + lane];
+      a1 += Li[d + INV_GROUP] * win[sd2 * 32 + lane];
+      sd = sd2 - INV_GROUP < 0 ? sd2 - INV_GROUP + W : sd2 - INV_GROUP;
+    }
+    if (d <= dmax) a0 += Li[d] * win[sd * 32 + lane];
+    double acc = a0 + a1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[i] = (y[i] - s) / L[(long long)i * n + i];
+    for (int o = 1; o < INV_GROUP; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const double y = ((i == j ? 1.0 : 0.0) - acc) * invL[i];
+    win[slot * 32 + lane] = y;
+    if (active && t == 0) Kinv[(size_t)i * n + j] = y;
+    slot = slot + 1 == W ? 0 : slot + 1;
+  }
+  __syncwarp();
+  for (int q = 0; q < W; ++q) win[q * 32 + lane] = 0.0;
+  __syncwarp();
+  // Backward substitution over all rows.
+  slot = (n - 1) % W;
+  for (int i = n - 1; i >= 0; --i) {
+    const double yi = (i >= j0 && active) ? Kinv[(size_t)i * n + j] : 0.0;
+    double a0 = 0.0, a1 = 0.0;
+    const int dmax = min(bw, n - 1 - i);
+    int d = 1 + t;
+    int sd = slot + d;
+    if (sd >= W) sd -= W;
+    for (; d + INV_GROUP <= dmax; d += 2 * INV_GROUP) {
+      const int sd2 = sd + INV_GROUP >= W ? sd + INV_GROUP - W : sd + INV_GROUP;
+      a0 += L[(size_t)(i + d) * W + d] * win[sd * 32 + lane];
+      a1 += L[(size_t)(i + d + INV_GROUP) * W + d + INV_GROUP] * win[sd2 * 32 + lane];
+      sd = sd2 + INV_GROUP >= W ? sd2 + INV_GROUP - W : sd2 + INV_GROUP;
+    }
+    if (d <= dmax) a0 += L[(size_t)(i + d) * W + d] * win[sd * 32 + lane];
+    double acc = a0 + a1;
+#pragma unroll
+    for (int o = 1; o < INV_GROUP; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const double x = (yi - acc) * invL[i];
+    win[slot * 32 + lane] = x;
     __syncwarp();
+    if (active && t == 0) Kinv[(size_t)i * n + j] = x;
+    slot = slot == 0 ? W - 1 : slot - 1;
   }
 }
 
@@ -394,25 +463,57 @@ template cudaError_t launch_coarse_invd<double>(const Grid&, const double*, doub
 template cudaError_t launch_coarse_invd<float>(const Grid&, const float*, double, float2*,
                                                cudaStream_t, int);
 
-cudaError_t launch_dense_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
-                                  double* Kd, cudaStream_t s) {
-  dense_assemble_kernel<<<(n + 127) / 128, 128, 0, s>>>(g, coef64, dof_index, n, Kd);
+cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
+                                 int bw, double* Kb, cudaStream_t s) {
+  band_assemble_kernel<<<(n + 127) / 128, 128, 0, s>>>(g, coef64, dof_index, n, bw, Kb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky_inverse(int n, int bw, double* Kd, double* Kinv, int* err_flag,
-                                    cudaStream_t s, int num_sms) {
+static int max_dyn_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
+                                    int* err_flag, cudaStream_t s, int num_sms) {
   (void)num_sms;
-  const size_t smem = sizeof(short2) * (size_t)bw * (bw + 1) / 2 + 16;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(cholesky_band_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int W = bw + 1;
+  const size_t pairs = sizeof(short2) * (size_t)bw * (bw + 1) / 2 + 16;
+  const size_t band = sizeof(double) * (size_t)n * W;
+  const int cap = max_dyn_smem();
+  cudaError_t e;
+  if (band + pairs <= (size_t)cap) {
+    e = cudaFuncSetAttribute(cholesky_band_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(band + pairs));
     if (e != cudaSuccess) return e;
+    cholesky_band_kernel<true><<<1, CHOL_NT, band + pairs, s>>>(n, bw, Kb, invL, err_flag);
+  } else {
+    if (pairs > 48 * 1024) {
+      e = cudaFuncSetAttribute(cholesky_band_kernel<false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pairs);
+      if (e != cudaSuccess) return e;
+    }
+    cholesky_band_kernel<false><<<1, CHOL_NT, pairs, s>>>(n, bw, Kb, invL, err_flag);
   }
-  cholesky_band_kernel<<<1, CHOL_NT, smem, s>>>(n, bw, Kd, err_flag);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  inverse_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, bw, Kd, Kinv);
+  const size_t win = sizeof(double) * (size_t)W * 32;
+  const int blocks = (n + INV_COLS - 1) / INV_COLS;
+  if (band + win <= (size_t)cap) {
+    e = cudaFuncSetAttribute(inverse_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(band + win));
+    if (e != cudaSuccess) return e;
+    inverse_cols_kernel<true><<<blocks, 32, band + win, s>>>(n, bw, Kb, invL, Kinv);
+  } else {
+    if (win > 48 * 1024) {
+      e = cudaFuncSetAttribute(inverse_cols_kernel<false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win);
+      if (e != cudaSuccess) return e;
+    }
+    inverse_cols_kernel<false><<<blocks, 32, win, s>>>(n, bw, Kb, invL, Kinv);
+  }
   return cudaGetLastError();
 }
 

@@ -46,7 +46,10 @@ constexpr int SWEEP_NT = 256;
 constexpr int SWEEP_STRIDE = 30;
 constexpr int SWEEP_RSTRIDE = 28;
 
-enum Src { SRC_FINE64 = 0, SRC_FINEBF = 1, SRC_COARSE = 2 };
+// SRC_CFINE: the first coarse level of the mixed path, whose Galerkin element
+// matrices are rebuilt on the fly from the four bf16 fine moduli they cover
+// (8 bytes per coarse element instead of 13 stored coefficients).
+enum Src { SRC_FINE64 = 0, SRC_FINEBF = 1, SRC_COARSE = 2, SRC_CFINE = 3 };
 enum Mode {
   MODE_APPLY = 0,
   MODE_RESID,
@@ -64,6 +67,7 @@ template <typename T> struct SweepParams {
   int nstrips, nchunks, H;
   int gate;          // 1: skip the launch once the PCG has stopped (sc->done)
   int replace_gate;  // RESID as residual replacement: run only when iter % rr_every == 0
+  int zero_gate;     // RESID of the initial guess: out = b when sc->x_nonzero == 0 (K 0 = 0)
   const T2* v;       // marched vector (z, x or p_old)
   const T2* zc;      // PSMOOTH: coarse correction
   const void* zkp;   // KP: z (double2 or float2)
@@ -74,7 +78,9 @@ template <typename T> struct SweepParams {
   const void* E;     // finest level: 4 scaled float64 moduli per element (FINE64) or bf16 E
   const T* coef;     // coarse element matrices, NCOEF arrays of g.size()
   long long cstride;
-  FineConst<T> kf;      // bf16 finest level: scale factors of the fine core
+  FineConst<T> kf;      // bf16 finest level / SRC_CFINE: scale factors of the element core
+  Grid gfine;           // SRC_CFINE: the finer grid whose bf16 moduli E points to
+  int redisc;           // SRC_CFINE: rediscretised (mean modulus) instead of Galerkin
   const double* invd1;  // float64 finest level: w / D per node
   const T2* invd2;      // coarse levels: w / D per DOF
   T wdiag;              // float32 finest level: w / (KE_00 at E = 1); D = sum of 4 moduli
@@ -128,6 +134,9 @@ template <typename T> struct ERaw<T, SRC_FINEBF> {
 };
 template <typename T> struct ERaw<T, SRC_COARSE> {
   T A[NCOEF];
+};
+template <typename T> struct ERaw<T, SRC_CFINE> {
+  __nv_bfloat162 lo, hi;  // fine moduli of rows 2J and 2J+1, columns 2I and 2I+1
 };
 
 // Loads that belong to the node row being completed.
@@ -192,8 +201,19 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
     }
   }
 
-  __device__ __forceinline__ static void load_e(const SweepParams<T>& a, long long e, ER& r) {
-    if constexpr (SRC == SRC_FINE64) {
+  __device__ __forceinline__ static void load_e(const SweepParams<T>& a, long long e, int ii, int jj,
+                                                ER& r) {
+    if constexpr (SRC == SRC_CFINE) {
+      // Ghost and padding elements have no children: zero operator.
+      if ((unsigned)ii < (unsigned)a.g.nx && (unsigned)jj < (unsigned)a.g.ny) {
+        const __nv_bfloat162* Ef = static_cast<const __nv_bfloat162*>(a.E);
+        const long long kf = a.gfine.at(2 * ii, 2 * jj);  // even: bf16 pairs are aligned
+        r.lo = Ef[kf >> 1];
+        r.hi = Ef[(kf + a.gfine.pitch) >> 1];
+      } else {
+        r.lo = r.hi = __floats2bfloat162_rn(0.f, 0.f);
+      }
+    } else if constexpr (SRC == SRC_FINE64) {
       const double2* p = static_cast<const double2*>(a.E) + 2 * e;
       r.k01 = __ldg(p);
       r.k23 = __ldg(p + 1);
@@ -209,7 +229,7 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
     if constexpr (NEEDS_B) r.b = a.b[k];
     if constexpr (SMOOTHING) {
       if constexpr (SRC == SRC_FINE64) r.d1 = a.invd1[k];
-      else if constexpr (SRC == SRC_COARSE) r.d2 = a.invd2[k];
+      else if constexpr (SRC == SRC_COARSE || SRC == SRC_CFINE) r.d2 = a.invd2[k];
       if constexpr (DOT) {
         r.rd = a.rdot[k];
         if (a.qdot != nullptr) r.qd = a.qdot[k];
@@ -231,6 +251,33 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
     } else if constexpr (SRC == SRC_FINEBF) {
       Ecur = __bfloat162float(er.E);
       t = fine_core<T>(w, Ecur, a.kf);
+    } else if constexpr (SRC == SRC_CFINE) {
+      // Moments of the four child moduli (children at xi, eta = +-1/2 of the
+      // parent): M00 = S/4, M10 = X/8, M01 = Y/8, M20 = M02 = M00/3,
+      // M11 = Z/16, then the 13 coefficients of mto_common.cuh.
+      const float2 l = __bfloat1622float2(er.lo), h = __bfloat1622float2(er.hi);
+      const T e00 = l.x, e10 = l.y, e01 = h.x, e11 = h.y;
+      const T M00 = T(0.25) * ((e00 + e10) + (e01 + e11));
+      T M10 = T(0.125) * ((e10 + e11) - (e00 + e01));
+      T M01 = T(0.125) * ((e01 + e11) - (e00 + e10));
+      T M11 = T(0.0625) * ((e00 + e11) - (e10 + e01));
+      if (a.redisc) M10 = M01 = M11 = T(0);
+      const FineConst<T> k = a.kf;  // kappa, kappa nu, kappa (1+g)/3, kappa g
+      T A[NCOEF];
+      A[0] = k.kA * M00;
+      A[1] = k.kA * M01;
+      A[2] = k.kC * M00;
+      A[3] = k.kA * M00;
+      A[4] = k.kA * M10;
+      A[5] = k.kC * M00;
+      A[6] = k.kB * M00;
+      A[7] = k.kB * M10;
+      A[8] = k.kB * M01;
+      A[9] = (k.kB + k.kG) * M11;
+      A[10] = k.kG * M00;
+      A[11] = k.kG * M10;
+      A[12] = k.kG * M01;
+      t = coarse_core<T>(w, A);
     } else {
       t = coarse_core<T>(w, er.A);
     }
@@ -256,8 +303,25 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
   double dot0 = 0.0, dot1 = 0.0;
   T beta = T(0);
   if constexpr (MODE == MODE_KP) beta = T(a.sc->beta);
+  bool vzero = false;
+  if constexpr (MODE == MODE_RESID) vzero = a.zero_gate && a.sc->x_nonzero == 0;
 
-  if (chunk < a.nchunks) {
+  if (vzero) {
+    // Residual of a zero iterate: r = b on the free DOFs, no operator needed.
+    if (chunk < a.nchunks) {
+      const Grid g = a.g;
+      const int i = strip * SWEEP_STRIDE - 1 + lane;
+      const bool own_col = lane >= 1 && lane <= 30 && i >= 0 && i <= g.nx;
+      const int r0 = chunk * a.H, r1 = min(r0 + a.H - 1, g.ny);
+      for (int j = r0; j <= r1 && own_col; ++j) {
+        const long long k = g.at(i, j);
+        T2 r = mk2<T>(T(0), T(0));
+        if (!g.is_fixed(i, j)) r = a.b[k];
+        a.out[k] = r;
+        dot0 += double(r.x) * double(r.x) + double(r.y) * double(r.y);
+      }
+    }
+  } else if (chunk < a.nchunks) {
     constexpr int STRIDE = MODE == MODE_RESTRICT ? SWEEP_RSTRIDE : SWEEP_STRIDE;
     constexpr int SHIFT = MODE == MODE_RESTRICT ? 2 : 1;
     const Grid g = a.g;
@@ -286,7 +350,7 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
     // Offsets of node (i, je + 1) and element / node (i, je) for step je.
     auto load_pack = [&](Pack& pk, int je, long long ke) {
       S::load_v(a, ke + pitch, i, je + 1, pk.vt);
-      S::load_e(a, ke, pk.e);
+      S::load_e(a, ke, i, je, pk.e);
       S::load_n(a, ke, pk.n);
     };
 
@@ -373,7 +437,7 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
               dx = dy = T(cur.n.d1);
             } else if constexpr (SRC == SRC_FINEBF) {
               dx = dy = __fdividef(a.wdiag, eo + eol);
-            } else {
+            } else {  // coarse levels: stored w / D
               dx = cur.n.d2.x;
               dy = cur.n.d2.y;
             }

@@ -32,6 +32,16 @@ cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepP
       default: return cudaErrorInvalidValue;
     }
   }
+  if (src == SRC_CFINE) {
+    switch (mode) {
+      case MODE_APPLY: return go<SRC_CFINE, MODE_APPLY, false, 2>(p, sh, s);
+      case MODE_SMOOTH: return go<SRC_CFINE, MODE_SMOOTH, false, 3>(p, sh, s);
+      case MODE_SMOOTH0: return go<SRC_CFINE, MODE_SMOOTH0, false, 3>(p, sh, s);
+      case MODE_PSMOOTH: return go<SRC_CFINE, MODE_PSMOOTH, false, 2>(p, sh, s);
+      case MODE_RESTRICT: return go<SRC_CFINE, MODE_RESTRICT, false, 3>(p, sh, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (src == SRC_COARSE) {
     switch (mode) {
       case MODE_APPLY: return go<SRC_COARSE, MODE_APPLY, false, 2>(p, sh, s);

@@ -116,8 +116,10 @@ __global__ void __launch_bounds__(VEC_NT)
   block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, finish, out_value);
 }
 
-__global__ void pack_kernel(Grid g, const double* __restrict__ src, double2* __restrict__ dst) {
+__global__ void pack_kernel(Grid g, const double* __restrict__ src, double2* __restrict__ dst,
+                            int* nonzero) {
   const long long n = g.size();
+  bool nz = false;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     int i, j;
@@ -126,9 +128,11 @@ __global__ void pack_kernel(Grid g, const double* __restrict__ src, double2* __r
     if (g.active(i, j)) {
       const long long s = 2 * ((long long)j * (g.nx + 1) + i);
       v = make_double2(src[s], src[s + 1]);
+      nz = nz || v.x != 0.0 || v.y != 0.0;
     }
     dst[k] = v;
   }
+  if (nonzero != nullptr && __any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0) atomicOr(nonzero, 1);
 }
 
 __global__ void unpack_kernel(Grid g, const double2* __restrict__ src, double* __restrict__ dst) {
@@ -194,8 +198,16 @@ __global__ void __launch_bounds__(GEMV_NT)
   const int row = blockIdx.x * (GEMV_NT / 32) + (threadIdx.x >> 5);
   if (row >= n) return;
   const double* kr = Kinv + (long long)row * n;
-  double acc = 0.0;
-  for (int k = lane; k < n; k += 32) acc += kr[k] * bs[k];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // independent chains
+  int k = lane;
+  for (; k + 96 < n; k += 128) {
+    a0 += kr[k] * bs[k];
+    a1 += kr[k + 32] * bs[k + 32];
+    a2 += kr[k + 64] * bs[k + 64];
+    a3 += kr[k + 96] * bs[k + 96];
+  }
+  for (; k < n; k += 32) a0 += kr[k] * bs[k];
+  double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) z[free_idx[row]] = (T)acc;
@@ -242,8 +254,9 @@ cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms) {
-  pack_kernel<<<vec_blocks(g.size(), num_sms), VEC_NT, 0, s>>>(g, src, dst);
+cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms,
+                        int* nonzero) {
+  pack_kernel<<<vec_blocks(g.size(), num_sms), VEC_NT, 0, s>>>(g, src, dst, nonzero);
   return cudaGetLastError();
 }
 cudaError_t launch_unpack(const Grid& g, const double2* src, double* dst, cudaStream_t s, int num_sms) {
