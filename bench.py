@@ -36,6 +36,10 @@ SEED = 0
 KP_OPS_PER_NODE = 36
 SMOOTH32_BYTES_PER_NODE = 26
 SMOOTH64_OPS_PER_NODE = 38  # K v 32, w D^-1 b 2, z + d (b - K v) 4 (first two sweeps fused)
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum,
+# profiles/sweeps_2048_ncu_full.md); None once the kernel changes.
+KP_TRAFFIC = None
+SMOOTH32_TRAFFIC = None
 # FP64 pipe: 2 operations per clock per SM (1.25 TFLOP/s nominal at 2 flops
 # per FMA), 152 SMs, 2070 MHz.
 FP64_OPS_PEAK = 2 * 152 * 2.070e9
@@ -53,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-size", type=int, default=512)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-outer", type=int, default=50)
     return ap.parse_args()
 
 
@@ -210,6 +217,101 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_batched(mto, dev, local):
+    """Batched workload: 32 square-wall problems, sizes drawn from {128,256,512,1024}^2
+    with seed 3, two load cases each (top -y, right +x), mixed path, one graph
+    launch per batch; next to it one float64 4096^2 solve."""
+    import numpy as np
+    import torch
+    from synth import batch_sizes, dirichlet_design, load_right_edge, load_top_edge
+
+    sizes = batch_sizes(32, seed=3)
+    problems = []
+    for k, s in enumerate(sizes):
+        nc = s.bit_length() - 1 - 4  # coarsest 16 x 16
+        m = mto.Mesh(s, s, n_coarsen=nc, precision="mixed", tol=1e-8, rr_every=25, flexible=True,
+                     device=local)
+        xk = torch.from_numpy(dirichlet_design(s, s, 4, seed=3000 + k)).to(dev)
+        F = torch.from_numpy(np.stack([load_top_edge(s, s), load_right_edge(s, s)])).to(dev)
+        m.set_design(xk, EP, PENAL)
+        m.autotune()
+        problems.append({"mesh": m, "x": xk, "E_phase": EP, "penal": PENAL, "f": F})
+    t0 = time.perf_counter()
+    batch = mto.Batch(problems)
+    build_ms = 1000 * (time.perf_counter() - t0)
+    def cold_run():
+        for pr in batch.problems:
+            pr["u"].zero_()  # every run solves from u = 0
+        return batch.run()
+
+    cold_run()  # warm-up
+    times, iters = [], 0
+    for _ in range(2):
+        st = cold_run()
+        times.append(batch.ms_last())
+        iters = sum(s["iters"] for s in st)
+    ms = min(times)
+    dof_iters = sum(ndof(pr["mesh"].nelx) * s["iters"] for pr, s in zip(problems, st))
+    out = {"problems": len(problems), "load_cases": 2 * len(problems),
+           "sizes": {str(s): sizes.count(s) for s in sorted(set(sizes))},
+           "ms_per_batch": ms, "load_cases_per_s": 2 * len(problems) / (ms / 1000.0),
+           "gdof_iter_s": dof_iters / (ms / 1000.0) / 1e9, "iters_total": iters,
+           "all_converged": all(s["converged"] == 1 for s in st), "graph_build_ms": build_ms,
+           "max_rel_res_true": max(s["rel_res_true"] for s in st)}
+    batch.close()
+    for pr in problems:
+        pr["mesh"].close()
+    # One float64 4096^2 solve (8 coarsenings to 16 x 16).
+    n4 = 4096
+    m4 = mto.Mesh(n4, n4, n_coarsen=8, precision="fp64", tol=1e-8, max_it=1000, device=local)
+    x4 = torch.from_numpy(dirichlet_design(n4, n4, 4, seed=3)).to(dev)
+    f4 = torch.from_numpy(load_top_edge(n4, n4)).to(dev)
+    m4.set_design(x4, EP, PENAL)
+    m4.autotune()
+    m4.solve(f4)
+    m4.set_design(x4, EP, PENAL)
+    u4, st4 = m4.solve(f4)
+    out["fp64_4096"] = {"dofs": ndof(n4), "iters": st4["iters"], "ms_solve": st4["ms_solve"],
+                        "ms_setup": st4["ms_setup"], "rel_res_true": st4["rel_res_true"],
+                        "gdof_iter_s": ndof(n4) * st4["iters"] / (st4["ms_solve"] / 1000.0) / 1e9}
+    m4.close()
+    del x4, f4, u4
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_sweep(mto, dev, local, n_outer):
+    """Mesh sweep: the alternating active-phase loop (float64 solves, each
+    warm-started from the previous u) at 256^2, 512^2, 1024^2 with 4, 5, 6
+    coarsenings and volume fractions [0.2, 0.15, 0.1] + void 0.55."""
+    import torch
+    from paper_2301_07457_gb300.optimize import ActivePhaseOptimizer
+    from synth import load_top_edge
+
+    out = {}
+    for n, nc in ((256, 4), (512, 5), (1024, 6)):
+        mesh = mto.Mesh(n, n, n_coarsen=nc, precision="fp64", tol=1e-8, max_it=1000, device=local)
+        f = torch.from_numpy(load_top_edge(n, n)).to(dev)
+        opt = ActivePhaseOptimizer(mesh, EP, [0.2, 0.15, 0.1, 0.55], f, penal=PENAL, rf=8.0)
+        opt.step()  # first outer iteration: cold start, tuning of the launch shapes
+        mesh.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        opt.run(n_outer - 1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        timed = opt.history[len(opt.pairs):]
+        its = [h[3] for h in timed]
+        out[str(n)] = {"outer_iterations": n_outer, "solves": len(opt.history),
+                       "s_timed": dt, "timed_solves": len(timed),
+                       "loop_solves_s": len(timed) / dt,
+                       "mean_pcg_iters_warm": sum(its) / len(its),
+                       "first_solve_iters": opt.history[0][3],
+                       "compliance_first": opt.history[0][2], "compliance_last": opt.history[-1][2]}
+        mesh.close()
+    return out
+
+
 def run_ours(args):
     import ctypes
 
@@ -261,13 +363,9 @@ def run_ours(args):
         C, g = mesh.compliance_grad(f, u)
         return st, C
 
-    def timed(mesh, steps, warmup, timing=False):
+    def timed(mesh, steps, warmup):
         for _ in range(warmup):
             step(mesh)
-        if timing:
-            _lib.check(mesh._lib.mto_set_kernel_timing(mesh._h, 1), "timing")
-            step(mesh)  # rebuild the graph with event nodes outside the timed region
-            _lib.check(mesh._lib.mto_set_kernel_timing(mesh._h, 1), "timing reset")
         torch.cuda.synchronize()
         barrier()
         l0 = launches(mesh)
@@ -282,17 +380,26 @@ def run_ours(args):
             torch.cuda.synchronize()
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1))
-        kt = None
-        if timing:
-            avg = (ctypes.c_double * 2)()
-            cnt = (ctypes.c_longlong * 2)()
-            _lib.check(mesh._lib.mto_get_kernel_times(mesh._h, avg, cnt), "kernel times")
-            kt = {"ms": [avg[0], avg[1]], "samples": [cnt[0], cnt[1]]}
-        return ms, stats, launches(mesh) - l0, clk.summary(), kt
+        return ms, stats, launches(mesh) - l0, clk.summary()
+
+    def kernel_times(mesh, steps):
+        # Events around the two hot kernels of every iteration (the solver
+        # then drives its loop from the host); a second timed region.
+        mesh.set_kernel_timing(True)
+        step(mesh)  # builds the graph with event nodes
+        mesh.set_kernel_timing(True)  # resets the sums
+        for _ in range(steps):
+            step(mesh)
+        t, cnt = mesh.kernel_times()
+        mesh.set_kernel_timing(False)
+        return {"ms": t, "samples": cnt}
 
     common = dict(n_coarsen=nc, tol=1e-8, max_it=1000, device=local)
     mixed = mto.Mesh(n, n, precision="mixed", rr_every=25, flexible=True, **common)
-    ms, stats, nlaunch, clocks, kt = timed(mixed, args.steps, args.warmup, timing=True)
+    mixed.set_design(x, EP, PENAL)
+    shapes_mixed = mixed.autotune()
+    ms, stats, nlaunch, clocks = timed(mixed, args.steps, args.warmup)
+    kt = kernel_times(mixed, 2)
     iters = [s["iters"] for s in stats]
     solve_ms = [s["ms_solve"] for s in stats]
     value = world * args.steps / (ms / 1000.0)
@@ -305,19 +412,22 @@ def run_ours(args):
     sm_bytes = SMOOTH32_BYTES_PER_NODE * nodes / (sm_ms / 1000.0)
     roofline = {"bound": "alu", "kernel": "outer sweep p=z+beta p, q=Kp, p.q (float64)",
                 "achieved": kp_ops / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-op/s",
-                "frac": kp_ops / FP64_OPS_PEAK, "traffic": None, "ms_per_launch": kp_ms,
+                "frac": kp_ops / FP64_OPS_PEAK, "traffic": KP_TRAFFIC, "ms_per_launch": kp_ms,
                 "samples": kt["samples"][0],
                 "peak_kind": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
     roofline_vcycle = {"bound": "hbm", "kernel": "finest damped-Jacobi sweep (float32, bf16 E)",
                        "achieved": sm_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                       "frac": sm_bytes / 1e9 / hbm_peak, "traffic": None, "ms_per_launch": sm_ms,
-                       "samples": kt["samples"][1], "peak_kind": peak_kind}
+                       "frac": sm_bytes / 1e9 / hbm_peak, "traffic": SMOOTH32_TRAFFIC,
+                       "ms_per_launch": sm_ms, "samples": kt["samples"][1], "peak_kind": peak_kind}
 
     # FP64 path on the same input.
     fp64 = None
     if args.fp64_steps > 0:
         m64 = mto.Mesh(n, n, precision="fp64", **common)
-        ms64, st64, _, clk64, kt64 = timed(m64, args.fp64_steps, 1, timing=True)
+        m64.set_design(x, EP, PENAL)
+        m64.autotune()
+        ms64, st64, _, clk64 = timed(m64, args.fp64_steps, 1)
+        kt64 = kernel_times(m64, 1)
         it64 = [s["iters"] for s in st64]
         v64 = world * args.fp64_steps / (ms64 / 1000.0)
         fp64 = {"solves_s": v64, "ms_per_step": ms64 / args.fp64_steps, "iters": it64,
@@ -327,6 +437,13 @@ def run_ours(args):
                 "smoother_fp64_frac_alu": SMOOTH64_OPS_PER_NODE * nodes / (kt64["ms"][1] / 1000.0) / FP64_OPS_PEAK,
                 "kp_fp64_frac_alu": KP_OPS_PER_NODE * nodes / (kt64["ms"][0] / 1000.0) / FP64_OPS_PEAK}
         m64.close()
+
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(mto, dev, local)
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(mto, dev, local, args.sweep_outer)
 
     # End to end through the C ABI with pinned host buffers.
     e2e = None
@@ -381,6 +498,7 @@ def run_ours(args):
         "ms_setup": stats[-1]["ms_setup"], "ms_solve": solve_ms,
         "fp64": fp64, "speedup_mixed_vs_fp64": (value / fp64["solves_s"]) if fp64 else None,
         "roofline": roofline, "roofline_vcycle": roofline_vcycle,
+        "launch_shapes": shapes_mixed, "batched": batched, "mesh_sweep": sweep,
         "clocks": clocks, "gpu_launches": nlaunch, "e2e": e2e, "cpu_baseline": cpu,
     }
     mixed.close()

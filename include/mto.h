@@ -115,6 +115,52 @@ mto_status mto_set_design(mto_ctx* ctx, int n_phase, const double* x_dev, const 
 mto_status mto_solve(mto_ctx* ctx, int n_rhs, const double* f_dev, double* u_dev,
                      mto_solve_stats* stats);
 
+/* Batched solves (independent problems of any mesh size in one CUDA graph).
+ * One context per problem; the contexts must differ, live on one device and
+ * not have kernel timing on.  Each item gives the problem's design and loads
+ * (same layouts and meanings as mto_set_design / mto_solve /
+ * mto_compliance_grad; E_phase is a host array, copied at creation; n_rhs <=
+ * 64; compliance_dev may be NULL, then dcdx_dev must be NULL too).
+ * mto_batch_create captures, per problem, set_design + one device-side PCG
+ * loop per load case (cold start from u_dev as given) + compliance into one
+ * branch of a graph; the device arrays named in the items are baked into it
+ * and must stay valid.  mto_batch_run launches the graph once on the stream
+ * given at creation (ordered after it, and it after the batch), waits for it
+ * and fills stats (host [n], may be NULL: iterations summed over the
+ * problem's load cases, residuals of its last one, ms_solve = device time of
+ * the whole batch).  Returns the worst status over the problems.
+ * mto_solve_batched is create + run + destroy in one call.  The paper solves
+ * one system at a time; batching is this library's extension (Sec. 4: the
+ * optimiser solves once per design update). */
+typedef struct mto_batch mto_batch;
+typedef struct {
+  int n_phase;
+  const double* x_dev;    /* device [n_phase][nely][nelx] */
+  const double* E_phase;  /* host [n_phase] */
+  double penal;
+  int n_rhs;
+  const double* f_dev;    /* device [n_rhs][nely+1][nelx+1][2] */
+  double* u_dev;          /* device, same layout: warm start in, solution out */
+  double* compliance_dev; /* device [n_rhs], may be NULL */
+  double* dcdx_dev;       /* device [n_phase][nely][nelx], may be NULL */
+} mto_batch_item;
+mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const mto_batch_item* items,
+                            void* cuda_stream);
+mto_status mto_batch_run(mto_batch* batch, mto_solve_stats* stats);
+mto_status mto_batch_time(mto_batch* batch, double* ms_last_run);
+void mto_batch_destroy(mto_batch* batch);
+mto_status mto_solve_batched(int n, mto_ctx* const* ctxs, const mto_batch_item* items,
+                             mto_solve_stats* stats, void* cuda_stream);
+
+/* Launch-shape tuner: for every level, times the marching sweep with several
+ * numbers of warps per launch (hence rows per warp task) on the device and
+ * keeps the fastest; results are cached for the process by (mesh size,
+ * precision, operator kind, SM count).  Needs a design (mto_set_design) and
+ * synchronises; later solves and batches use the chosen shapes.
+ * mto_get_launch_shape returns the chosen (or default) warps per launch. */
+mto_status mto_autotune(mto_ctx* ctx);
+mto_status mto_get_launch_shape(mto_ctx* ctx, int level, int* target_warps);
+
 /* Statistics of the last mto_solve (synchronises the context's stream). */
 mto_status mto_last_stats(mto_ctx* ctx, mto_solve_stats* stats);
 

@@ -26,7 +26,7 @@ from ._lib import (  # noqa: F401
     SolveStats,
 )
 
-__all__ = ["Mesh", "Compliance", "compliance", "MtoError", "SolverOpts", "SolveStats"]
+__all__ = ["Mesh", "Batch", "Compliance", "compliance", "MtoError", "SolverOpts", "SolveStats"]
 
 
 def _ptr(t):
@@ -187,11 +187,105 @@ class Mesh:
         _lib.check(code, "mto_apply_preconditioner")
         return z
 
+    def autotune(self):
+        """Time launch shapes on the device and keep the fastest per level."""
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.mto_autotune(self._h), "mto_autotune")
+        return [self.launch_shape(l) for l in range(self.opts.n_coarsen + 1)]
+
+    def launch_shape(self, level):
+        t = ctypes.c_int()
+        _lib.check(self._lib.mto_get_launch_shape(self._h, level, ctypes.byref(t)), "mto_get_launch_shape")
+        return t.value
+
+    def set_kernel_timing(self, enable):
+        _lib.check(self._lib.mto_set_kernel_timing(self._h, int(enable)), "mto_set_kernel_timing")
+
+    def kernel_times(self):
+        avg = (ctypes.c_double * 2)()
+        cnt = (ctypes.c_longlong * 2)()
+        _lib.check(self._lib.mto_get_kernel_times(self._h, avg, cnt), "mto_get_kernel_times")
+        return list(avg), list(cnt)
+
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        _lib.check(self._lib.mto_get_launch_count(self._h, ctypes.byref(c)), "mto_get_launch_count")
+        return c.value
+
     def moduli(self):
         E = torch.empty((self.nely, self.nelx), dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
             _lib.check(self._lib.mto_get_moduli(self._h, _ptr(E)), "mto_get_moduli")
         return E
+
+
+class Batch:
+    """Independent problems (one Mesh each, any sizes) solved by one graph launch.
+
+    problems: list of dicts with keys mesh, x, E_phase, penal (default 3),
+    f ([n_rhs][ny+1][nx+1][2] or [ny+1][nx+1][2]), optional u0.  The outputs
+    (u, compliance, dcdx per problem) are device tensors owned by the batch
+    and refreshed by every run().
+    """
+
+    def __init__(self, problems, want_grad=True):
+        lib = _lib.load()
+        self._lib = lib
+        self.problems = []
+        n = len(problems)
+        items = (_lib.BatchItem * n)()
+        ctxs = (ctypes.c_void_p * n)()
+        self._keep = []
+        dev = problems[0]["mesh"].device
+        for i, pr in enumerate(problems):
+            mesh = pr["mesh"]
+            x = _dev_f64(pr["x"], mesh.device, "x")
+            f = _dev_f64(pr["f"], mesh.device, "f")
+            if f.dim() == 3:
+                f = f.unsqueeze(0)
+            u = torch.zeros_like(f) if pr.get("u0") is None else _dev_f64(pr["u0"], mesh.device, "u0").clone()
+            C = torch.zeros(f.shape[0], dtype=torch.float64, device=mesh.device)
+            g = torch.zeros(x.shape, dtype=torch.float64, device=mesh.device) if want_grad else None
+            E = (ctypes.c_double * len(pr["E_phase"]))(*[float(e) for e in pr["E_phase"]])
+            it = items[i]
+            it.n_phase, it.x_dev, it.E_phase, it.penal = x.shape[0], x.data_ptr(), E, float(pr.get("penal", 3.0))
+            it.n_rhs, it.f_dev, it.u_dev = f.shape[0], f.data_ptr(), u.data_ptr()
+            it.compliance_dev = C.data_ptr()
+            it.dcdx_dev = g.data_ptr() if g is not None else None
+            ctxs[i] = mesh._h.value
+            self._keep += [x, f, E]
+            self.problems.append({"mesh": mesh, "u": u, "compliance": C, "dcdx": g, "x": x, "f": f})
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            code = lib.mto_batch_create(ctypes.byref(self._h), n, ctxs, items, _stream(dev))
+        _lib.check(code, "mto_batch_create")
+        self.device = dev
+
+    def run(self, raise_on_failure=True):
+        n = len(self.problems)
+        st = (SolveStats * n)()
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_batch_run(self._h, st)
+        if code not in (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_BREAKDOWN) or (
+                raise_on_failure and code != _lib.OK):
+            _lib.check(code, "mto_batch_run")
+        return [s.as_dict() for s in st]
+
+    def ms_last(self):
+        v = ctypes.c_double()
+        _lib.check(self._lib.mto_batch_time(self._h, ctypes.byref(v)), "mto_batch_time")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.mto_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Compliance(torch.autograd.Function):

@@ -60,6 +60,20 @@ class SolveStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("n_phase", ctypes.c_int),
+        ("x_dev", ctypes.c_void_p),
+        ("E_phase", ctypes.POINTER(ctypes.c_double)),
+        ("penal", ctypes.c_double),
+        ("n_rhs", ctypes.c_int),
+        ("f_dev", ctypes.c_void_p),
+        ("u_dev", ctypes.c_void_p),
+        ("compliance_dev", ctypes.c_void_p),
+        ("dcdx_dev", ctypes.c_void_p),
+    ]
+
+
 class MtoError(RuntimeError):
     def __init__(self, code, where=""):
         self.code = code
@@ -87,6 +101,15 @@ SIGNATURES = {
     "mto_compliance_grad_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                                    _P, _D, ctypes.c_double, _P, _P, _P, _P, ctypes.c_int,
                                                    _P]),
+    "mto_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
+                                        ctypes.POINTER(BatchItem), _P]),
+    "mto_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(SolveStats)]),
+    "mto_batch_time": (ctypes.c_int, [_P, _D]),
+    "mto_batch_destroy": (None, [_P]),
+    "mto_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(BatchItem),
+                                         ctypes.POINTER(SolveStats), _P]),
+    "mto_autotune": (ctypes.c_int, [_P]),
+    "mto_get_launch_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mto_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "mto_get_kernel_times": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),

@@ -1,120 +1,26 @@
 // C ABI of libmto: context and memory plan, per-design setup, the PCG driver
 // (Alg. 2) with its V-cycle preconditioner (Alg. 1), compliance and
 // sensitivities, and the diagnostic entry points.
+//
+// A solve is one CUDA graph: the PCG loop runs on the device inside a
+// conditional WHILE node whose body holds two iterations; the last kernel of
+// the body keeps the loop going while the device scalars say "running".  No
+// host round trip happens inside a solve.  With kernel timing on, the loop is
+// driven from the host instead (graph of two iterations, polled), because
+// event records cannot live inside a conditional body.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "mto.h"
-#include "mto_launch.h"
+#include "mto_ctx.cuh"
 
 using namespace mto;
 
-namespace {
-
-struct LevelBuf {
-  Grid g{};
-  void* z[2] = {nullptr, nullptr};  // V2<T> vectors (ping-pong)
-  void* b = nullptr;                // right-hand side of this level
-  void* coef = nullptr;             // T coefficients, NCOEF * g.size()
-  void* invd2 = nullptr;            // V2<T> w / D
-  double* mom = nullptr;            // NMOM * g.size() (coarse levels)
-  double* coef64 = nullptr;         // level 0: float64 coefficients for the dense matrix
-};
-
-}  // namespace
-
-struct mto_ctx {
-  int device = 0, num_sms = 1;
-  cudaStream_t user_stream = nullptr, stream = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
-  int nelx = 0, nely = 0;
-  double nu = 0.3;
-  unsigned fixed = 0;
-  mto_solver_opts o{};
-  int L = 0;
-  bool mixed = false;
-  std::vector<LevelBuf> lv;
-  // finest level
-  double* E64 = nullptr;
-  double* Ek4 = nullptr;  // E (kA, kB, kC, kG) per element, for the float64 sweeps
-  __nv_bfloat16* Ebf = nullptr;
-  double* invd1 = nullptr;
-  double2 *x = nullptr, *r = nullptr, *q = nullptr, *f = nullptr, *tmp = nullptr;
-  double2* p[2] = {nullptr, nullptr};
-  float2* r32 = nullptr;
-  // coarsest grid
-  int n0 = 0, bw0 = 0;
-  int* dof_index = nullptr;
-  double *Kd = nullptr, *Kinv = nullptr, *invL = nullptr;  // Kd: band storage of K_0 / its factor
-  int* err_flag = nullptr;
-  // reductions
-  double* partials = nullptr;
-  unsigned* ticket = nullptr;
-  DevScalars* sc = nullptr;
-  DevScalars* sc_host = nullptr;  // pinned
-  int* err_host = nullptr;        // pinned
-  // design
-  bool has_design = false;
-  int n_phase = 0;
-  PhaseTable ph{};
-  double penal = 3.0;
-  int ipenal = 3;
-  double* xdes = nullptr;
-  size_t xdes_cap = 0;
-  // host-call staging (mto_run_host)
-  double *hx = nullptr, *hf = nullptr, *hu = nullptr, *hc = nullptr, *hg = nullptr;
-  size_t hx_cap = 0, hf_cap = 0, hg_cap = 0;
-  int hc_cap = 0;
-  // graph of two PCG iterations
-  cudaGraphExec_t gexec = nullptr;
-  long long graph_kernels = 0;  // kernel nodes in the graph
-  long long launches = 0;       // kernels launched by this context (graph nodes included)
-  // optional event pairs around the hot kernels of each graph iteration:
-  // [parity][0 = outer K p sweep, 1 = first finest-level smoothing sweep][start, end]
-  bool timing = false;
-  cudaEvent_t kev[2][2][2] = {};
-  double ksum[2] = {0.0, 0.0};
-  long long kcnt[2] = {0, 0};
-  int cur_par = -1;
-  // constants
-  FineConst<double> kf64{};
-  FineConst<float> kf32{};
-  double w_over_kdiag = 0.0;
-  // stats
-  float ms_setup = 0.f;
-  mto_solve_stats last{};
-  std::vector<void*> allocs;
-};
+thread_local cudaError_t mto::g_last_cuda = cudaSuccess;
 
 namespace {
-
-// Last CUDA error that made a call of this thread return MTO_ERR_CUDA.
-thread_local cudaError_t g_last_cuda = cudaSuccess;
-
-#define CK(call)                    \
-  do {                              \
-    cudaError_t e_ = (call);        \
-    if (e_ != cudaSuccess) {        \
-      g_last_cuda = e_;             \
-      return MTO_ERR_CUDA;          \
-    }                               \
-  } while (0)
-
-// A kernel launch made by the context: counted, then checked.
-#define KL(call)              \
-  do {                        \
-    c->launches += 1;         \
-    CK(call);                 \
-  } while (0)
-
-#define ST(call)                          \
-  do {                                    \
-    mto_status s_ = (call);               \
-    if (s_ != MTO_OK) return s_;          \
-  } while (0)
 
 mto_status dalloc(mto_ctx* c, void** out, size_t bytes) {
   *out = nullptr;
@@ -140,6 +46,7 @@ mto_status enter(mto_ctx* c) {
   CK(cudaSetDevice(c->device));
   CK(cudaEventRecord(c->ev_in, c->user_stream));
   CK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  c->cs = c->stream;
   return MTO_OK;
 }
 mto_status leave(mto_ctx* c) {
@@ -148,7 +55,29 @@ mto_status leave(mto_ctx* c) {
   return MTO_OK;
 }
 
-int target_warps(const mto_ctx* c) { return c->num_sms * 32; }
+}  // namespace
+
+namespace mto {
+
+int target_warps(const mto_ctx* c, int level) {
+  const int t = (level >= 0 && level < MAX_LEVELS) ? c->tw[level] : 0;
+  return t > 0 ? t : c->num_sms * DEFAULT_TARGET_WARPS_PER_SM;
+}
+
+int target_warps64(const mto_ctx* c) {
+  return c->tw64 > 0 ? c->tw64 : target_warps(c, c->L);
+}
+
+void invalidate_graphs(mto_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  c->gexec = nullptr;
+  c->solve_exec = nullptr;
+}
+
+}  // namespace mto
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // Sweep helpers
@@ -164,12 +93,10 @@ template <typename T> SweepParams<T> base_params(const mto_ctx* c, const Grid& g
 }
 
 template <typename T> FineConst<T> fine_const(const mto_ctx* c);
-
-// SRC_CFINE parameters: the finest bf16 moduli and their grid.
-template <typename T> void set_cfine(const mto_ctx* c, SweepParams<T>& p);
 template <> FineConst<double> fine_const<double>(const mto_ctx* c) { return c->kf64; }
 template <> FineConst<float> fine_const<float>(const mto_ctx* c) { return c->kf32; }
 
+// SRC_CFINE parameters: the finest bf16 moduli and their grid.
 template <typename T> void set_cfine(const mto_ctx* c, SweepParams<T>& p) {
   p.E = c->Ebf;
   p.gfine = c->lv[c->L].g;
@@ -184,7 +111,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   using T2 = typename V2<T>::t;
   LevelBuf& L = c->lv[l];
   LevelBuf& C = c->lv[l - 1];
-  const int tw = target_warps(c);
+  const int tw = target_warps(c, l);
   const int nb = vec_blocks(L.g.size(), c->num_sms);
   int cur = 0;
   // The first coarse level of the mixed path rebuilds its element matrices
@@ -205,7 +132,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     p.coef = (const T*)L.coef;
     p.invd2 = (const T2*)L.invd2;
     if (cfine) set_cfine(c, p);
-    return launch_sweep<T>(src, mode, false, false, p, sweep_shape(L.g, mode, tw), c->stream);
+    return launch_sweep<T>(src, mode, false, false, p, sweep_shape(L.g, mode, tw), c->cs);
   };
   // Pre-smoothing from U = 0: the first sweep (U = w D^-1 F) is formed on the
   // fly inside the second when there are two or more.
@@ -213,7 +140,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr));
   } else {
     KL(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb,
-                                c->stream));
+                                c->cs));
   }
   for (int s = 2; s < c->o.nu1; ++s) {
     KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
@@ -223,7 +150,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   int cidx = 0;
   if (l - 1 == 0) {
     KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
-                               (T2*)C.z[0], sc, c->stream));
+                               (T2*)C.z[0], sc, c->cs));
   } else {
     ST(coarse_cycle<T>(c, l - 1, sc, &cidx));
   }
@@ -246,7 +173,7 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   constexpr bool MIX = sizeof(T) == 4;
   LevelBuf& L = c->lv[c->L];
   LevelBuf& C = c->lv[c->L - 1];
-  const int tw = target_warps(c);
+  const int tw = target_warps(c, c->L);
   const int nb = vec_blocks(L.g.size(), c->num_sms);
   const int src = MIX ? SRC_FINEBF : SRC_FINE64;
   const T2* b;
@@ -255,10 +182,10 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   const bool fused0 = !MIX && c->o.nu1 >= 2;
   if constexpr (MIX) {
     KL(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r, c->r32, (float2*)L.z[0], sc,
-                             nb, c->stream));
+                             nb, c->cs));
     b = (const T2*)c->r32;
   } else {
-    if (!fused0) KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->stream));
+    if (!fused0) KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->cs));
     b = (const T2*)c->r;
   }
   int cur = 0;
@@ -281,16 +208,16 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
       p.qdot = c->o.flexible ? c->q : nullptr;
       p.finish = FIN_RHO;
     }
-    return launch_sweep<T>(src, mode, dot, false, p, sweep_shape(L.g, mode, tw), c->stream);
+    return launch_sweep<T>(src, mode, dot, false, p, sweep_shape(L.g, mode, tw), c->cs);
   };
   // Timing events bracket the first finest-level smoothing kernel.
   const bool tm = c->timing && sc != nullptr && c->cur_par >= 0;
   auto t0 = [&]() -> cudaError_t {
-    return tm ? cudaEventRecordWithFlags(c->kev[c->cur_par][1][0], c->stream, cudaEventRecordExternal)
+    return tm ? cudaEventRecordWithFlags(c->kev[c->cur_par][1][0], c->cs, cudaEventRecordExternal)
               : cudaSuccess;
   };
   auto t1 = [&]() -> cudaError_t {
-    return tm ? cudaEventRecordWithFlags(c->kev[c->cur_par][1][1], c->stream, cudaEventRecordExternal)
+    return tm ? cudaEventRecordWithFlags(c->kev[c->cur_par][1][1], c->cs, cudaEventRecordExternal)
               : cudaSuccess;
   };
   int first = 1;
@@ -310,7 +237,7 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   int cidx = 0;
   if (c->L - 1 == 0) {
     KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
-                               (T2*)C.z[0], sc, c->stream));
+                               (T2*)C.z[0], sc, c->cs));
   } else {
     ST(coarse_cycle<T>(c, c->L - 1, sc, &cidx));
   }
@@ -341,7 +268,7 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.E = c->Ek4;
   p.finish = finish;
   KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
-                          sweep_shape(g, MODE_RESID, target_warps(c)), c->stream));
+                          sweep_shape(g, MODE_RESID, target_warps64(c)), c->cs));
   return MTO_OK;
 }
 
@@ -350,16 +277,15 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
   const Grid& g = c->lv[c->L].g;
   c->cur_par = par;
   int zi = 0;
-  const void* z;
   if (c->mixed) {
     ST(fine_cycle<float>(c, c->sc, true, &zi));
   } else {
     ST(fine_cycle<double>(c, c->sc, true, &zi));
   }
-  z = c->lv[c->L].z[zi];
+  const void* z = c->lv[c->L].z[zi];
   // External event-record nodes inside the captured graph (a plain record
   // during capture would only mark a dependency).
-  if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][0], c->stream, cudaEventRecordExternal));
+  if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][0], c->cs, cudaEventRecordExternal));
   {
     SweepParams<double> p = base_params<double>(c, g);
     p.gate = 1;
@@ -371,18 +297,20 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.E = c->Ek4;
     p.finish = FIN_PQ;
     KL(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
-                            sweep_shape(g, MODE_KP, target_warps(c)), c->stream));
+                            sweep_shape(g, MODE_KP, target_warps64(c)), c->cs));
   }
-  if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->stream, cudaEventRecordExternal));
+  if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->cs, cudaEventRecordExternal));
   KL(launch_update(g, c->x, c->r, c->p[par ^ 1], c->q, c->partials, c->ticket, c->sc,
-                   vec_blocks(g.size(), c->num_sms), c->stream));
+                   vec_blocks(g.size(), c->num_sms), c->cs));
   if (c->mixed && c->o.rr_every > 0) ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1));
   return MTO_OK;
 }
 
-mto_status build_graph(mto_ctx* c) {
+// Graph of two iterations for the host-polled loop.
+mto_status build_poll_graph(mto_ctx* c) {
   if (c->gexec) return MTO_OK;
   cudaGraph_t graph = nullptr;
+  c->cs = c->stream;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   const long long before = c->launches;
   mto_status s0 = enqueue_iteration(c, 0);
@@ -396,41 +324,56 @@ mto_status build_graph(mto_ctx* c) {
     cudaGetLastError();
     return s1;
   }
-  if (e != cudaSuccess) return MTO_ERR_CUDA;
+  if (e != cudaSuccess) {
+    g_last_cuda = e;
+    return MTO_ERR_CUDA;
+  }
   e = cudaGraphInstantiate(&c->gexec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     c->gexec = nullptr;
+    g_last_cuda = e;
     return MTO_ERR_CUDA;
   }
   return MTO_OK;
 }
 
-bool valid_opts(const mto_solver_opts& o) {
-  return o.tol >= 0.0 && o.max_it >= 0 && o.omega > 0.0 && o.omega <= 1.0 && o.nu1 >= 1 &&
-         o.nu2 >= 1 && o.nu1 <= 16 && o.nu2 <= 16 && o.n_coarsen >= 1 && o.n_coarsen <= 14 &&
-         (o.coarse_kind == MTO_COARSE_GALERKIN || o.coarse_kind == MTO_COARSE_REDISCRETIZE) &&
-         (o.precision == MTO_PRECISION_FP64 || o.precision == MTO_PRECISION_MIXED) &&
-         o.rr_every >= 0 && o.check_every >= 1;
+// Graph of a whole solve (everything after the packing of f and u).
+mto_status build_solve_graph(mto_ctx* c) {
+  if (c->solve_exec) return MTO_OK;
+  cudaGraph_t graph = nullptr;
+  c->cs = c->stream;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = c->launches;
+  mto_status s = enqueue_solve_core(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  c->solve_kernels_fixed = c->launches - before;
+  c->launches = before;
+  c->cs = c->stream;
+  if (s != MTO_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (s == MTO_OK) g_last_cuda = e;
+    return s != MTO_OK ? s : MTO_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&c->solve_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->solve_exec = nullptr;
+    g_last_cuda = e;
+    return MTO_ERR_CUDA;
+  }
+  return MTO_OK;
 }
 
-mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_out) {
+// Host-polled solve loop (kernel timing mode, or no conditional nodes).
+mto_status solve_polled(mto_ctx* c) {
   const Grid& g = c->lv[c->L].g;
-  DevScalars s0;
-  std::memset(&s0, 0, sizeof(s0));
-  s0.tol2 = c->o.tol * c->o.tol;
-  s0.max_it = c->o.max_it;
-  s0.flexible = c->o.flexible;
-  s0.rr_every = c->mixed ? c->o.rr_every : 0;
-  *c->sc_host = s0;
-  CK(cudaMemcpyAsync(c->sc, c->sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
-  KL(launch_pack(g, f_dev, c->f, c->stream, c->num_sms));
-  KL(launch_pack(g, u_dev, c->x, c->stream, c->num_sms, &c->sc->x_nonzero));
   CK(cudaMemsetAsync(c->p[0], 0, sizeof(double2) * g.size(), c->stream));
   KL(launch_dot(g.size(), c->f, c->f, c->partials, c->ticket, c->sc, FIN_FF, nullptr,
                 vec_blocks(g.size(), c->num_sms), c->stream));
   ST(fine_resid(c, c->x, c->f, c->r, FIN_INIT_RR, 0, 0, 1));
-  ST(build_graph(c));
+  ST(build_poll_graph(c));
   const int poll = (c->o.check_every + 1) / 2;  // graph launches (2 iterations each) per poll
   int launched = 0;
   for (;;) {
@@ -457,19 +400,242 @@ mto_status solve_one(mto_ctx* c, const double* f_dev, double* u_dev, int* iters_
     }
   }
   ST(fine_resid(c, c->x, c->f, c->tmp, FIN_TRUE, 0, 0));
-  KL(launch_unpack(g, c->x, u_dev, c->stream, c->num_sms));
-  CK(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  const DevScalars& h = *c->sc_host;
-  const double fn = std::sqrt(h.ff);
-  c->last.iters = h.iter;
-  c->last.converged = h.done == CONVERGED;
-  c->last.rel_res_rec = fn > 0 ? std::sqrt(h.rr) / fn : 0.0;
-  c->last.rel_res_true = fn > 0 ? std::sqrt(h.rr_true) / fn : 0.0;
-  *iters_out = h.iter;
-  if (h.done == BREAKDOWN) return MTO_ERR_BREAKDOWN;
-  if (h.done != CONVERGED) return MTO_ERR_NOT_CONVERGED;
   return MTO_OK;
+}
+
+bool valid_opts(const mto_solver_opts& o) {
+  return o.tol >= 0.0 && o.max_it >= 0 && o.omega > 0.0 && o.omega <= 1.0 && o.nu1 >= 1 &&
+         o.nu2 >= 1 && o.nu1 <= 16 && o.nu2 <= 16 && o.n_coarsen >= 1 && o.n_coarsen <= 14 &&
+         (o.coarse_kind == MTO_COARSE_GALERKIN || o.coarse_kind == MTO_COARSE_REDISCRETIZE) &&
+         (o.precision == MTO_PRECISION_FP64 || o.precision == MTO_PRECISION_MIXED) &&
+         o.rr_every >= 0 && o.check_every >= 1;
+}
+
+mto_status status_of(const RhsStats& r) {
+  if (r.done == BREAKDOWN) return MTO_ERR_BREAKDOWN;
+  if (r.done != CONVERGED) return MTO_ERR_NOT_CONVERGED;
+  return MTO_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Enqueue functions shared with the batch driver (capturable: no host sync).
+// ===========================================================================
+namespace mto {
+
+mto_status enqueue_solve_core(mto_ctx* c) {
+  const Grid& g = c->lv[c->L].g;
+  CK(cudaMemsetAsync(c->p[0], 0, sizeof(double2) * g.size(), c->cs));
+  KL(launch_dot(g.size(), c->f, c->f, c->partials, c->ticket, c->sc, FIN_FF, nullptr,
+                vec_blocks(g.size(), c->num_sms), c->cs));
+  ST(fine_resid(c, c->x, c->f, c->r, FIN_INIT_RR, 0, 0, 1));
+  // Device-side loop: a conditional WHILE node after the current capture
+  // dependencies, its body captured on the body stream.
+  cudaStreamCaptureStatus st;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c->cs, &st, nullptr, &graph, &deps, &edges, &nd));
+  if (st != cudaStreamCaptureStatusActive) return MTO_ERR_STATE;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, graph, deps, edges, nd, &np));
+  CK(cudaStreamUpdateCaptureDependencies(c->cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t outer = c->cs;
+  CK(cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  c->cs = c->body_stream;
+  const long long before = c->launches;
+  mto_status s = enqueue_iteration(c, 0);
+  if (s == MTO_OK) s = enqueue_iteration(c, 1);
+  if (s == MTO_OK) {
+    c->launches += 1;
+    const cudaError_t e = launch_set_continue(h, c->sc, c->cs);
+    if (e != cudaSuccess) {
+      g_last_cuda = e;
+      s = MTO_ERR_CUDA;
+    }
+  }
+  c->cur_par = -1;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->body_stream, &captured);
+  c->cs = outer;
+  c->body_kernels = c->launches - before;
+  c->launches = before;
+  if (s != MTO_OK) return s;
+  if (e != cudaSuccess) {
+    g_last_cuda = e;
+    return MTO_ERR_CUDA;
+  }
+  ST(fine_resid(c, c->x, c->f, c->tmp, FIN_TRUE, 0, 0));
+  return MTO_OK;
+}
+
+mto_status enqueue_rhs_prologue(mto_ctx* c, const double* f_dev, const double* u_dev) {
+  const Grid& g = c->lv[c->L].g;
+  KL(launch_init_scalars(c->sc, c->o.tol * c->o.tol, c->o.max_it, c->o.flexible,
+                         c->mixed ? c->o.rr_every : 0, c->cs));
+  KL(launch_pack(g, f_dev, c->f, c->cs, c->num_sms));
+  KL(launch_pack(g, u_dev, c->x, c->cs, c->num_sms, &c->sc->x_nonzero));
+  return MTO_OK;
+}
+
+mto_status enqueue_rhs_epilogue(mto_ctx* c, double* u_dev, int rhs_slot) {
+  const Grid& g = c->lv[c->L].g;
+  KL(launch_unpack(g, c->x, u_dev, c->cs, c->num_sms));
+  KL(launch_record_stats(c->sc, c->rhs_stats + rhs_slot, c->cs));
+  return MTO_OK;
+}
+
+mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
+                              double penal) {
+  const Grid& gf = c->lv[c->L].g;
+  const size_t nel = (size_t)c->nelx * c->nely;
+  if (c->xdes_cap < (size_t)n_phase * nel) return MTO_ERR_STATE;  // grown by the caller
+  c->n_phase = n_phase;
+  for (int i = 0; i < 16; ++i) c->ph.E[i] = i < n_phase ? E_phase[i] : 0.0;
+  c->penal = penal;
+  c->ipenal = (penal == std::floor(penal) && penal <= 16.0) ? (int)penal : -1;
+  CK(cudaMemcpyAsync(c->xdes, x_dev, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice, c->cs));
+  KL(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->Ek4, c->kf64,
+                    c->cs, c->num_sms));
+  if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->cs, c->num_sms));
+  const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
+  for (int l = c->L - 1; l >= 0; --l) {
+    LevelBuf& B = c->lv[l];
+    if (l == c->L - 1) {
+      KL(launch_moments_from_fine(B.g, gf, c->mixed ? nullptr : c->E64, c->mixed ? c->Ebf : nullptr,
+                                  redisc, B.mom, c->cs, c->num_sms));
+    } else {
+      KL(launch_moments_from_coarse(B.g, c->lv[l + 1].g, c->lv[l + 1].mom, redisc, B.mom, c->cs,
+                                    c->num_sms));
+    }
+    if (c->mixed) {
+      KL(launch_coefs<float>(B.g, B.mom, c->nu, (float*)B.coef, c->cs, c->num_sms));
+      if (l > 0)
+        KL(launch_coarse_invd<float>(B.g, (const float*)B.coef, c->o.omega, (float2*)B.invd2, c->cs,
+                                     c->num_sms));
+    } else {
+      KL(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->cs, c->num_sms));
+      if (l > 0)
+        KL(launch_coarse_invd<double>(B.g, (const double*)B.coef, c->o.omega, (double2*)B.invd2,
+                                      c->cs, c->num_sms));
+    }
+  }
+  LevelBuf& B0 = c->lv[0];
+  KL(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->cs, c->num_sms));
+  CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * (c->bw0 + 1), c->cs));
+  CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->cs));
+  KL(launch_band_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->bw0, c->Kd, c->cs));
+  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Kinv, c->err_flag, c->cs,
+                             c->num_sms));
+  c->launches += 1;  // the inverse is a second kernel
+  return MTO_OK;
+}
+
+mto_status enqueue_compliance(mto_ctx* c, int n_rhs, const double* f_dev, const double* u_dev,
+                              double* compliance_dev, double* dcdx_dev) {
+  const long long nn = (long long)(c->nelx + 1) * (c->nely + 1);
+  for (int k = 0; k < n_rhs; ++k) {
+    const double2* fk = reinterpret_cast<const double2*>(f_dev + 2 * nn * k);
+    const double2* uk = reinterpret_cast<const double2*>(u_dev + 2 * nn * k);
+    KL(launch_dot(nn, fk, uk, c->partials, c->ticket, nullptr, FIN_NONE, compliance_dev + k,
+                  vec_blocks(nn, c->num_sms), c->cs));
+    if (dcdx_dev)
+      KL(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
+                            c->kf64, u_dev + 2 * nn * k, dcdx_dev, k > 0, c->cs, c->num_sms));
+  }
+  return MTO_OK;
+}
+
+}  // namespace mto
+
+namespace {
+
+mto_status grow(mto_ctx* c, double** p, size_t* cap, size_t need) {
+  if (*cap >= need) return MTO_OK;
+  ST(dalloc_t(c, p, need));
+  *cap = need;
+  return MTO_OK;
+}
+
+mto_status set_design_sync(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
+                           double penal) {
+  const size_t nel = (size_t)c->nelx * c->nely;
+  ST(grow(c, &c->xdes, &c->xdes_cap, (size_t)n_phase * nel));
+  c->cs = c->stream;
+  CK(cudaEventRecord(c->ev_a, c->stream));
+  ST(enqueue_set_design(c, n_phase, x_dev, E_phase, penal));
+  CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaEventRecord(c->ev_b, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaEventElapsedTime(&c->ms_setup, c->ev_a, c->ev_b));
+  if (*c->err_host) return MTO_ERR_BREAKDOWN;
+  c->has_design = true;
+  return MTO_OK;
+}
+
+// Solves right-hand sides [0, n_rhs) and fills c->last; one host sync.
+mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) {
+  const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
+  c->cs = c->stream;
+  const bool polled = c->timing || c->no_while;
+  if (!polled) {
+    const mto_status b = build_solve_graph(c);
+    if (b != MTO_OK) {
+      // Conditional graph nodes unavailable: fall back to the polled loop.
+      c->no_while = true;
+      cudaGetLastError();
+    }
+  }
+  CK(cudaEventRecord(c->ev_a, c->stream));
+  for (int k = 0; k < n_rhs; ++k) {
+    c->cs = c->stream;
+    ST(enqueue_rhs_prologue(c, f_dev + k * nd, u_dev + k * nd));
+    if (c->timing || c->no_while) {
+      ST(solve_polled(c));
+    } else {
+      CK(cudaGraphLaunch(c->solve_exec, c->stream));
+      c->launches += c->solve_kernels_fixed;
+    }
+    ST(enqueue_rhs_epilogue(c, u_dev + k * nd, k));
+  }
+  CK(cudaEventRecord(c->ev_b, c->stream));
+  CK(cudaMemcpyAsync(c->rhs_stats_host, c->rhs_stats, sizeof(RhsStats) * n_rhs,
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+  mto_status worst = MTO_OK;
+  int total = 0;
+  for (int k = 0; k < n_rhs; ++k) {
+    const RhsStats& r = c->rhs_stats_host[k];
+    total += r.iter;
+    if (!(c->timing || c->no_while)) {
+      // The loop body (two iterations) ran max(1, ceil(iter / 2)) times.
+      const long long bodies = r.iter > 0 ? (r.iter + 1) / 2 : 1;
+      c->launches += c->body_kernels * bodies;
+    }
+    const mto_status s = status_of(r);
+    if (s != MTO_OK && worst == MTO_OK) worst = s;
+  }
+  const RhsStats& r = c->rhs_stats_host[n_rhs - 1];
+  const double fn = std::sqrt(r.ff);
+  c->last.iters = total;
+  c->last.converged = worst == MTO_OK;
+  c->last.rel_res_rec = fn > 0 ? std::sqrt(r.rr) / fn : 0.0;
+  c->last.rel_res_true = fn > 0 ? std::sqrt(r.rr_true) / fn : 0.0;
+  c->last.ms_solve = ms;
+  c->last.ms_setup = c->ms_setup;
+  return worst;
 }
 
 }  // namespace
@@ -516,10 +682,11 @@ void mto_destroy(mto_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  invalidate_graphs(c);
   for (void* p : c->allocs) cudaFree(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->rhs_stats_host) cudaFreeHost(c->rhs_stats_host);
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b)
       for (int d = 0; d < 2; ++d)
@@ -528,6 +695,7 @@ void mto_destroy(mto_ctx* c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->body_stream) cudaStreamDestroy(c->body_stream);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -546,12 +714,15 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   CK(cudaSetDevice(device));
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
   CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking));
+  c->cs = c->stream;
   CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
   CK(cudaEventCreate(&c->ev_a));
   CK(cudaEventCreate(&c->ev_b));
   CK(cudaMallocHost(&c->sc_host, sizeof(DevScalars)));
   CK(cudaMallocHost(&c->err_host, sizeof(int)));
+  CK(cudaMallocHost(&c->rhs_stats_host, sizeof(RhsStats) * MAX_RHS));
 
   // Element-operator constants (plane stress, Eq. 8; strain basis, mto_common.cuh).
   const double kap = 1.0 / (4.0 * (1.0 - nu * nu)), gs = 0.5 * (1.0 - nu);
@@ -560,6 +731,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   const double kdiag = kap * (1.0 + (1.0 + gs) / 3.0 + gs);  // KE_00 at E = 1
   c->w_over_kdiag = o.omega / kdiag;
 
+  if (c->L + 1 > MAX_LEVELS) return MTO_ERR_UNSUPPORTED_MESH;
   c->lv.resize(c->L + 1);
   for (int l = 0; l <= c->L; ++l) {
     const int sh = c->L - l;
@@ -641,12 +813,16 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   // Reduction scratch: two partials per block of the largest launch.
   int maxb = vec_blocks(gf.size(), c->num_sms);
   for (int mode = 0; mode <= MODE_RESTRICT; ++mode) {
-    const SweepShape s = sweep_shape(gf, mode, target_warps(c));
+    const SweepShape s = sweep_shape(gf, mode, MAX_TARGET_WARPS_PER_SM * c->num_sms);
     if (s.nblocks > maxb) maxb = s.nblocks;
   }
   ST(dalloc_t(c, &c->partials, 2 * (size_t)maxb + 2));
   ST(dalloc_t(c, &c->ticket, 4));
   ST(dalloc_t(c, &c->sc, 1));
+  ST(dalloc_t(c, &c->rhs_stats, MAX_RHS));
+  // Opt-in shared memory of the coarsest factorisation, set once here so that
+  // set_design can be captured into graphs.
+  CK(prepare_cholesky_inverse(c->n0, c->bw0));
   return MTO_OK;
 }
 
@@ -674,105 +850,36 @@ mto_status mto_create_mesh(mto_ctx** out, int nelx, int nely, double nu, unsigne
   return MTO_OK;
 }
 
-static mto_status set_design_impl(mto_ctx* c, int n_phase, const double* x_dev,
-                                  const double* E_phase, double penal) {
-  const Grid& gf = c->lv[c->L].g;
-  const size_t nel = (size_t)c->nelx * c->nely;
-  if (c->xdes_cap < (size_t)n_phase * nel) {
-    ST(dalloc_t(c, &c->xdes, (size_t)n_phase * nel));
-    c->xdes_cap = (size_t)n_phase * nel;
-  }
-  c->n_phase = n_phase;
-  for (int i = 0; i < 16; ++i) c->ph.E[i] = i < n_phase ? E_phase[i] : 0.0;
-  c->penal = penal;
-  c->ipenal = (penal == std::floor(penal) && penal <= 16.0) ? (int)penal : -1;
-  CK(cudaEventRecord(c->ev_a, c->stream));
-  CK(cudaMemcpyAsync(c->xdes, x_dev, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice,
-                     c->stream));
-  KL(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->Ek4, c->kf64,
-                    c->stream, c->num_sms));
-  if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->stream, c->num_sms));
-  const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
-  for (int l = c->L - 1; l >= 0; --l) {
-    LevelBuf& B = c->lv[l];
-    if (l == c->L - 1) {
-      KL(launch_moments_from_fine(B.g, gf, c->mixed ? nullptr : c->E64, c->mixed ? c->Ebf : nullptr,
-                                  redisc, B.mom, c->stream, c->num_sms));
-    } else {
-      KL(launch_moments_from_coarse(B.g, c->lv[l + 1].g, c->lv[l + 1].mom, redisc, B.mom, c->stream,
-                                    c->num_sms));
-    }
-    if (c->mixed) {
-      KL(launch_coefs<float>(B.g, B.mom, c->nu, (float*)B.coef, c->stream, c->num_sms));
-      if (l > 0)
-        KL(launch_coarse_invd<float>(B.g, (const float*)B.coef, c->o.omega, (float2*)B.invd2,
-                                     c->stream, c->num_sms));
-    } else {
-      KL(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->stream, c->num_sms));
-      if (l > 0)
-        KL(launch_coarse_invd<double>(B.g, (const double*)B.coef, c->o.omega, (double2*)B.invd2,
-                                      c->stream, c->num_sms));
-    }
-  }
-  LevelBuf& B0 = c->lv[0];
-  KL(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->stream, c->num_sms));
-  CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * (c->bw0 + 1), c->stream));
-  CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->stream));
-  KL(launch_band_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->bw0, c->Kd, c->stream));
-  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Kinv, c->err_flag, c->stream,
-                             c->num_sms));
-  c->launches += 1;  // the inverse is a second kernel
-  CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaEventRecord(c->ev_b, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  CK(cudaEventElapsedTime(&c->ms_setup, c->ev_a, c->ev_b));
-  if (*c->err_host) return MTO_ERR_BREAKDOWN;
-  c->has_design = true;
-  return MTO_OK;
+static bool valid_design(int n_phase, const double* E_phase, double penal) {
+  if (!E_phase || n_phase < 1 || n_phase > 16 || !(penal >= 1.0 && penal <= 64.0)) return false;
+  for (int i = 0; i < n_phase; ++i)
+    if (!(E_phase[i] > 0.0 && E_phase[i] < 1e300)) return false;
+  return true;
 }
 
 mto_status mto_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
                           double penal) {
-  if (!c || !x_dev || !E_phase || n_phase < 1 || n_phase > 16 || !(penal >= 1.0 && penal <= 64.0))
-    return MTO_ERR_ARG;
-  for (int i = 0; i < n_phase; ++i)
-    if (!(E_phase[i] > 0.0 && E_phase[i] < 1e300)) return MTO_ERR_ARG;
+  if (!c || !x_dev || !valid_design(n_phase, E_phase, penal)) return MTO_ERR_ARG;
   ST(enter(c));
   c->has_design = false;
-  mto_status s = set_design_impl(c, n_phase, x_dev, E_phase, penal);
+  mto_status s = set_design_sync(c, n_phase, x_dev, E_phase, penal);
   mto_status s2 = leave(c);
   return s != MTO_OK ? s : s2;
 }
 
 mto_status mto_solve(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev,
                      mto_solve_stats* stats) {
-  if (!c || n_rhs < 1 || !f_dev || !u_dev) return MTO_ERR_ARG;
+  if (!c || n_rhs < 1 || n_rhs > MAX_RHS || !f_dev || !u_dev) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
-  const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
-  mto_status worst = MTO_OK;
-  int total_it = 0;
-  CK(cudaEventRecord(c->ev_a, c->stream));
-  for (int k = 0; k < n_rhs; ++k) {
-    int it = 0;
-    mto_status s = solve_one(c, f_dev + k * nd, u_dev + k * nd, &it);
-    total_it += it;
-    if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM) {
-      leave(c);
-      return s;
-    }
-    if (s != MTO_OK && worst == MTO_OK) worst = s;
+  const mto_status s = solve_rhs(c, n_rhs, f_dev, u_dev);
+  if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM || s == MTO_ERR_STATE) {
+    leave(c);
+    return s;
   }
-  CK(cudaEventRecord(c->ev_b, c->stream));
-  CK(cudaEventSynchronize(c->ev_b));
-  float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
-  c->last.iters = total_it;
-  c->last.ms_solve = ms;
-  c->last.ms_setup = c->ms_setup;
   ST(leave(c));
   if (stats) *stats = c->last;
-  return worst;
+  return s;
 }
 
 mto_status mto_last_stats(mto_ctx* c, mto_solve_stats* stats) {
@@ -788,31 +895,15 @@ mto_status mto_compliance_grad(mto_ctx* c, int n_rhs, const double* f_dev, const
   if (!c || n_rhs < 1 || !f_dev || !u_dev || !compliance_dev) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
-  const long long nn = (long long)(c->nelx + 1) * (c->nely + 1);
-  for (int k = 0; k < n_rhs; ++k) {
-    const double2* fk = reinterpret_cast<const double2*>(f_dev + 2 * nn * k);
-    const double2* uk = reinterpret_cast<const double2*>(u_dev + 2 * nn * k);
-    KL(launch_dot(nn, fk, uk, c->partials, c->ticket, nullptr, FIN_NONE, compliance_dev + k,
-                  vec_blocks(nn, c->num_sms), c->stream));
-    if (dcdx_dev)
-      KL(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
-                            c->kf64, u_dev + 2 * nn * k, dcdx_dev, k > 0, c->stream, c->num_sms));
-  }
+  ST(enqueue_compliance(c, n_rhs, f_dev, u_dev, compliance_dev, dcdx_dev));
   return leave(c);
-}
-
-static mto_status grow(mto_ctx* c, double** p, size_t* cap, size_t need) {
-  if (*cap >= need) return MTO_OK;
-  ST(dalloc_t(c, p, need));
-  *cap = need;
-  return MTO_OK;
 }
 
 mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const double* E_phase,
                         double penal, int n_rhs, const double* f_host, double* u_host,
                         double* compliance_host, double* dcdx_host, mto_solve_stats* stats) {
-  if (!c || !x_host || !E_phase || n_rhs < 1 || !f_host || !u_host || !compliance_host ||
-      n_phase < 1 || n_phase > 16)
+  if (!c || !x_host || n_rhs < 1 || n_rhs > MAX_RHS || !f_host || !u_host || !compliance_host ||
+      !valid_design(n_phase, E_phase, penal))
     return MTO_ERR_ARG;
   const size_t nel = (size_t)c->nelx * c->nely;
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
@@ -829,12 +920,11 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
   CK(cudaMemcpyAsync(c->hf, f_host, sizeof(double) * n_rhs * nd, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->hu, 0, sizeof(double) * n_rhs * nd, c->stream));
   c->has_design = false;
-  ST(set_design_impl(c, n_phase, c->hx, E_phase, penal));
-  // The context's stream is already ordered after the caller's; solve and
-  // compliance re-enter harmlessly.
-  mto_status s = mto_solve(c, n_rhs, c->hf, c->hu, stats);
-  if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM) return s;
-  ST(mto_compliance_grad(c, n_rhs, c->hf, c->hu, c->hc, dcdx_host ? c->hg : nullptr));
+  ST(set_design_sync(c, n_phase, c->hx, E_phase, penal));
+  const mto_status s = solve_rhs(c, n_rhs, c->hf, c->hu);
+  if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM || s == MTO_ERR_STATE) return s;
+  c->cs = c->stream;
+  ST(enqueue_compliance(c, n_rhs, c->hf, c->hu, c->hc, dcdx_host ? c->hg : nullptr));
   CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * n_rhs * nd, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(compliance_host, c->hc, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, c->stream));
   if (dcdx_host)
@@ -842,6 +932,7 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
                        c->stream));
   CK(cudaStreamSynchronize(c->stream));
   ST(leave(c));
+  if (stats) *stats = c->last;
   return s;
 }
 
@@ -851,19 +942,19 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   LevelBuf& B = c->lv[level];
-  const int tw = target_warps(c);
+  const int tw = target_warps(c, level);
   const bool fine = level == c->L;
   if (fine && (!c->mixed || !use_vcycle_operator)) {
-    KL(launch_pack(B.g, v_dev, c->tmp, c->stream, c->num_sms));
+    KL(launch_pack(B.g, v_dev, c->tmp, c->cs, c->num_sms));
     SweepParams<double> p = base_params<double>(c, B.g);
     p.v = c->tmp;
     p.out = c->q;
     p.E = c->Ek4;
     KL(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
-                            sweep_shape(B.g, MODE_APPLY, tw), c->stream));
-    KL(launch_unpack(B.g, c->q, y_dev, c->stream, c->num_sms));
+                            sweep_shape(B.g, MODE_APPLY, tw), c->cs));
+    KL(launch_unpack(B.g, c->q, y_dev, c->cs, c->num_sms));
   } else if (c->mixed) {
-    KL(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->stream, c->num_sms));
+    KL(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->cs, c->num_sms));
     SweepParams<float> p = base_params<float>(c, B.g);
     p.v = (const float2*)B.z[0];
     p.out = (float2*)B.z[1];
@@ -873,17 +964,17 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     const bool cfine = level == c->L - 1;
     if (cfine) set_cfine(c, p);
     KL(launch_sweep<float>(fine ? SRC_FINEBF : (cfine ? SRC_CFINE : SRC_COARSE), MODE_APPLY, false,
-                           false, p, sweep_shape(B.g, MODE_APPLY, tw), c->stream));
-    KL(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->stream, c->num_sms));
+                           false, p, sweep_shape(B.g, MODE_APPLY, tw), c->cs));
+    KL(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->cs, c->num_sms));
   } else {
-    KL(launch_pack(B.g, v_dev, (double2*)B.z[0], c->stream, c->num_sms));
+    KL(launch_pack(B.g, v_dev, (double2*)B.z[0], c->cs, c->num_sms));
     SweepParams<double> p = base_params<double>(c, B.g);
     p.v = (const double2*)B.z[0];
     p.out = (double2*)B.z[1];
     p.coef = (const double*)B.coef;
     KL(launch_sweep<double>(SRC_COARSE, MODE_APPLY, false, false, p,
-                            sweep_shape(B.g, MODE_APPLY, tw), c->stream));
-    KL(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->stream, c->num_sms));
+                            sweep_shape(B.g, MODE_APPLY, tw), c->cs));
+    KL(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->cs, c->num_sms));
   }
   return leave(c);
 }
@@ -893,14 +984,14 @@ mto_status mto_apply_preconditioner(mto_ctx* c, const double* r_dev, double* z_d
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   LevelBuf& B = c->lv[c->L];
-  KL(launch_pack(B.g, r_dev, c->r, c->stream, c->num_sms));
+  KL(launch_pack(B.g, r_dev, c->r, c->cs, c->num_sms));
   int zi = 0;
   if (c->mixed) {
     ST(fine_cycle<float>(c, nullptr, false, &zi));
-    KL(launch_unpack_f32(B.g, (const float2*)B.z[zi], z_dev, c->stream, c->num_sms));
+    KL(launch_unpack_f32(B.g, (const float2*)B.z[zi], z_dev, c->cs, c->num_sms));
   } else {
     ST(fine_cycle<double>(c, nullptr, false, &zi));
-    KL(launch_unpack(B.g, (const double2*)B.z[zi], z_dev, c->stream, c->num_sms));
+    KL(launch_unpack(B.g, (const double2*)B.z[zi], z_dev, c->cs, c->num_sms));
   }
   return leave(c);
 }
@@ -916,22 +1007,19 @@ mto_status mto_get_moduli(mto_ctx* c, double* E_dev) {
   if (!c || !E_dev) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
-  KL(launch_unpack_elems(c->lv[c->L].g, c->E64, E_dev, c->stream, c->num_sms));
+  KL(launch_unpack_elems(c->lv[c->L].g, c->E64, E_dev, c->cs, c->num_sms));
   return leave(c);
 }
 
 mto_status mto_set_kernel_timing(mto_ctx* c, int enable) {
   if (!c) return MTO_ERR_ARG;
   CK(cudaSetDevice(c->device));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaStreamSynchronize(c->cs));
   if (enable && !c->kev[0][0][0])
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b)
         for (int d = 0; d < 2; ++d) CK(cudaEventCreate(&c->kev[a][b][d]));
-  if ((bool)enable != c->timing && c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  if ((bool)enable != c->timing) invalidate_graphs(c);
   c->timing = enable != 0;
   c->ksum[0] = c->ksum[1] = 0.0;
   c->kcnt[0] = c->kcnt[1] = 0;

@@ -1,0 +1,374 @@
+// Batched solves in one CUDA graph, and the launch-shape tuner.
+//
+// A batch is a set of independent problems (designs of any mesh size, each
+// with its own load cases), one context per problem.  mto_batch_create
+// captures, for every problem, set_design + one device-side PCG loop per
+// load case + compliance/sensitivities as one branch of a single graph; the
+// branches have no dependencies between them, so small meshes run side by
+// side on the GPU.  mto_batch_run is one graph launch: no host round trip
+// until the whole batch is done.
+//
+// The tuner picks, per level, how many warps a marching sweep exposes (the
+// rows per warp task follow from it) by timing candidates on the device.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "mto_ctx.cuh"
+
+using namespace mto;
+
+struct mto_batch {
+  int device = 0;
+  std::vector<mto_ctx*> ctx;
+  std::vector<mto_batch_item> items;
+  std::vector<std::vector<double>> E_phase;  // host copies of the phase moduli
+  cudaStream_t user_stream = nullptr, origin = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr, fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+  long long fixed_kernels = 0;
+  float ms_last = 0.f;
+};
+
+namespace {
+
+void destroy_batch(mto_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_a, b->ev_b, b->fork})
+    if (e) cudaEventDestroy(e);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+mto_status grow_design(mto_ctx* c, int n_phase) {
+  const size_t need = (size_t)n_phase * c->nelx * c->nely;
+  if (c->xdes_cap >= need) return MTO_OK;
+  void* p = nullptr;
+  if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return MTO_ERR_OOM;
+  }
+  c->allocs.push_back(p);
+  c->xdes = static_cast<double*>(p);
+  c->xdes_cap = need;
+  return MTO_OK;
+}
+
+// One branch of the batch graph: everything a problem needs, on its context's
+// stream (which joined the capture through the fork event).
+mto_status capture_branch(mto_ctx* c, const mto_batch_item& it, const double* E_phase) {
+  const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
+  c->cs = c->stream;
+  ST(enqueue_set_design(c, it.n_phase, it.x_dev, E_phase, it.penal));
+  for (int k = 0; k < it.n_rhs; ++k) {
+    ST(enqueue_rhs_prologue(c, it.f_dev + k * nd, it.u_dev + k * nd));
+    ST(enqueue_solve_core(c));
+    ST(enqueue_rhs_epilogue(c, it.u_dev + k * nd, k));
+  }
+  if (it.compliance_dev)
+    ST(enqueue_compliance(c, it.n_rhs, it.f_dev, it.u_dev, it.compliance_dev, it.dcdx_dev));
+  return MTO_OK;
+}
+
+// Launch shapes already measured in this process: (nx, ny, float32?, source,
+// SM count) -> best target warps.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+
+}  // namespace
+
+extern "C" {
+
+mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const mto_batch_item* items,
+                            void* cuda_stream) {
+  if (!out || n < 1 || !ctxs || !items) return MTO_ERR_ARG;
+  *out = nullptr;
+  const int device = ctxs[0] ? ctxs[0]->device : -1;
+  for (int i = 0; i < n; ++i) {
+    mto_ctx* c = ctxs[i];
+    const mto_batch_item& it = items[i];
+    if (!c || c->device != device || c->timing) return MTO_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return MTO_ERR_ARG;  // a context has one set of buffers
+    if (!it.x_dev || !it.E_phase || !it.f_dev || !it.u_dev || it.n_rhs < 1 || it.n_rhs > MAX_RHS ||
+        it.n_phase < 1 || it.n_phase > 16 || !(it.penal >= 1.0 && it.penal <= 64.0) ||
+        (it.dcdx_dev && !it.compliance_dev))
+      return MTO_ERR_ARG;
+    for (int p = 0; p < it.n_phase; ++p)
+      if (!(it.E_phase[p] > 0.0 && it.E_phase[p] < 1e300)) return MTO_ERR_ARG;
+  }
+  mto_batch* b = new (std::nothrow) mto_batch();
+  if (!b) return MTO_ERR_OOM;
+  b->device = device;
+  b->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  b->ctx.assign(ctxs, ctxs + n);
+  b->items.assign(items, items + n);
+  for (int i = 0; i < n; ++i) b->E_phase.emplace_back(items[i].E_phase, items[i].E_phase + items[i].n_phase);
+  auto fail = [&](mto_status s) {
+    destroy_batch(b);
+    cudaGetLastError();
+    return s;
+  };
+#define BK(call)                         \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) {             \
+      g_last_cuda = e_;                  \
+      return fail(MTO_ERR_CUDA);         \
+    }                                    \
+  } while (0)
+  BK(cudaSetDevice(device));
+  BK(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
+  BK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+  BK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  BK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  BK(cudaEventCreate(&b->ev_a));
+  BK(cudaEventCreate(&b->ev_b));
+  b->join.resize(n, nullptr);
+  for (int i = 0; i < n; ++i) BK(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+  for (int i = 0; i < n; ++i) {
+    const mto_status s = grow_design(b->ctx[i], items[i].n_phase);
+    if (s != MTO_OK) return fail(s);
+    BK(cudaStreamSynchronize(b->ctx[i]->stream));
+  }
+  // Capture: fork from the origin stream to every context's stream, join back.
+  cudaGraph_t graph = nullptr;
+  BK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+  mto_status st = MTO_OK;
+  long long fixed = 0;
+  cudaError_t ce = cudaEventRecord(b->fork, b->origin);
+  for (int i = 0; i < n && st == MTO_OK && ce == cudaSuccess; ++i) {
+    mto_ctx* c = b->ctx[i];
+    ce = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    if (ce != cudaSuccess) break;
+    const long long before = c->launches;
+    st = capture_branch(c, b->items[i], b->E_phase[i].data());
+    fixed += c->launches - before;
+    c->launches = before;
+    if (st == MTO_OK) ce = cudaEventRecord(b->join[i], c->stream);
+    if (st == MTO_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+  }
+  const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+  for (mto_ctx* c : b->ctx) c->cs = c->stream;
+  if (st != MTO_OK || ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (st == MTO_OK) g_last_cuda = ce != cudaSuccess ? ce : ee;
+    return fail(st != MTO_OK ? st : MTO_ERR_CUDA);
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    b->exec = nullptr;
+    g_last_cuda = ie;
+    return fail(MTO_ERR_CUDA);
+  }
+  b->fixed_kernels = fixed;
+#undef BK
+  *out = b;
+  return MTO_OK;
+}
+
+mto_status mto_batch_run(mto_batch* b, mto_solve_stats* stats) {
+  if (!b) return MTO_ERR_ARG;
+  CK(cudaSetDevice(b->device));
+  CK(cudaEventRecord(b->ev_in, b->user_stream));
+  CK(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+  CK(cudaEventRecord(b->ev_a, b->origin));
+  CK(cudaGraphLaunch(b->exec, b->origin));
+  CK(cudaEventRecord(b->ev_b, b->origin));
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    mto_ctx* c = b->ctx[i];
+    CK(cudaMemcpyAsync(c->rhs_stats_host, c->rhs_stats, sizeof(RhsStats) * b->items[i].n_rhs,
+                       cudaMemcpyDeviceToHost, b->origin));
+    CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, b->origin));
+  }
+  CK(cudaEventRecord(b->ev_out, b->origin));
+  CK(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0));
+  CK(cudaStreamSynchronize(b->origin));
+  CK(cudaEventElapsedTime(&b->ms_last, b->ev_a, b->ev_b));
+  mto_status worst = MTO_OK;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    mto_ctx* c = b->ctx[i];
+    const int nr = b->items[i].n_rhs;
+    int total = 0;
+    bool ok = *c->err_host == 0;
+    for (int k = 0; k < nr; ++k) {
+      const RhsStats& r = c->rhs_stats_host[k];
+      total += r.iter;
+      c->launches += c->body_kernels * (r.iter > 0 ? (r.iter + 1) / 2 : 1);
+      if (r.done != CONVERGED) ok = false;
+      if (r.done == BREAKDOWN && worst == MTO_OK) worst = MTO_ERR_BREAKDOWN;
+    }
+    if (*c->err_host && worst == MTO_OK) worst = MTO_ERR_BREAKDOWN;
+    if (!ok && worst == MTO_OK) worst = MTO_ERR_NOT_CONVERGED;
+    const RhsStats& r = c->rhs_stats_host[nr - 1];
+    const double fn = std::sqrt(r.ff);
+    c->last.iters = total;
+    c->last.converged = ok;
+    c->last.rel_res_rec = fn > 0 ? std::sqrt(r.rr) / fn : 0.0;
+    c->last.rel_res_true = fn > 0 ? std::sqrt(r.rr_true) / fn : 0.0;
+    c->last.ms_solve = b->ms_last;
+    c->last.ms_setup = 0.0;
+    c->has_design = *c->err_host == 0;
+    if (stats) stats[i] = c->last;
+  }
+  // Kernels outside the loop bodies, credited to the first context.
+  b->ctx[0]->launches += b->fixed_kernels;
+  return worst;
+}
+
+void mto_batch_destroy(mto_batch* b) { destroy_batch(b); }
+
+mto_status mto_solve_batched(int n, mto_ctx* const* ctxs, const mto_batch_item* items,
+                             mto_solve_stats* stats, void* cuda_stream) {
+  mto_batch* b = nullptr;
+  ST(mto_batch_create(&b, n, ctxs, items, cuda_stream));
+  const mto_status s = mto_batch_run(b, stats);
+  destroy_batch(b);
+  return s;
+}
+
+mto_status mto_batch_time(mto_batch* b, double* ms) {
+  if (!b || !ms) return MTO_ERR_ARG;
+  *ms = b->ms_last;
+  return MTO_OK;
+}
+
+}  // extern "C"
+
+// Mean device time of `reps` launches of `launch` after one warm-up launch.
+template <typename F> static mto_status time_launches(mto_ctx* c, F launch, int reps, double* ms) {
+  CK(launch());
+  CK(cudaEventRecord(c->ev_a, c->stream));
+  for (int r = 0; r < reps; ++r) CK(launch());
+  CK(cudaEventRecord(c->ev_b, c->stream));
+  CK(cudaEventSynchronize(c->ev_b));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, c->ev_a, c->ev_b));
+  *ms = t / reps;
+  return MTO_OK;
+}
+
+static const int kTuneCand[] = {4, 8, 16, 32, 64, 128};
+
+// The fastest candidate for one kind of sweep; `make` launches it with a
+// given target-warp count.
+template <typename F>
+static mto_status tune_one(mto_ctx* c, const std::tuple<int, int, int, int, int>& key, F make, int* out) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto hit = g_tune_cache.find(key);
+    if (hit != g_tune_cache.end()) {
+      *out = hit->second;
+      return MTO_OK;
+    }
+  }
+  double best_ms = 1e30;
+  int best = c->num_sms * DEFAULT_TARGET_WARPS_PER_SM;
+  for (int m : kTuneCand) {
+    const int tw = m * c->num_sms;
+    double ms = 0.0;
+    ST(time_launches(c, [&]() { return make(tw); }, 10, &ms));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tw;
+    }
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = best;
+  *out = best;
+  return MTO_OK;
+}
+
+extern "C" mto_status mto_autotune(mto_ctx* c) {
+  if (!c) return MTO_ERR_ARG;
+  if (!c->has_design) return MTO_ERR_STATE;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cs = c->stream;
+  // V-cycle sweeps: a damped-Jacobi sweep of each level in the V-cycle's
+  // precision (z[0] -> z[1], scratch), the kernel that dominates the cycle.
+  for (int l = 1; l <= c->L; ++l) {
+    LevelBuf& B = c->lv[l];
+    const bool f32 = c->mixed;
+    const bool fine = l == c->L;
+    const int src = fine ? (f32 ? SRC_FINEBF : SRC_FINE64)
+                         : (f32 && l == c->L - 1 ? SRC_CFINE : SRC_COARSE);
+    auto make = [&](int tw) -> cudaError_t {
+      if (f32) {
+        SweepParams<float> p;
+        std::memset(&p, 0, sizeof(p));
+        p.g = B.g;
+        p.cstride = B.g.size();
+        p.v = (const float2*)B.z[0];
+        p.out = (float2*)B.z[1];
+        p.b = fine ? (const float2*)c->r32 : (const float2*)B.b;
+        p.E = c->Ebf;
+        p.kf = c->kf32;
+        p.wdiag = (float)c->w_over_kdiag;
+        p.coef = (const float*)B.coef;
+        p.invd2 = (const float2*)B.invd2;
+        if (src == SRC_CFINE) {
+          p.gfine = c->lv[c->L].g;
+          p.redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
+        }
+        return launch_sweep<float>(src, MODE_SMOOTH, false, false, p, sweep_shape(B.g, MODE_SMOOTH, tw),
+                                   c->stream);
+      }
+      SweepParams<double> p;
+      std::memset(&p, 0, sizeof(p));
+      p.g = B.g;
+      p.cstride = B.g.size();
+      p.v = (const double2*)B.z[0];
+      p.out = (double2*)B.z[1];
+      p.b = fine ? c->r : (const double2*)B.b;
+      p.E = c->Ek4;
+      p.invd1 = c->invd1;
+      p.coef = (const double*)B.coef;
+      p.invd2 = (const double2*)B.invd2;
+      return launch_sweep<double>(src, MODE_SMOOTH, false, false, p, sweep_shape(B.g, MODE_SMOOTH, tw),
+                                  c->stream);
+    };
+    ST(tune_one(c, std::make_tuple(B.g.nx, B.g.ny, (int)f32, src, c->num_sms), make, &c->tw[l]));
+  }
+  // float64 outer sweeps of the finest level (K p and residuals): K v on
+  // scratch vectors (x -> tmp).
+  {
+    const Grid& g = c->lv[c->L].g;
+    auto make = [&](int tw) -> cudaError_t {
+      SweepParams<double> p;
+      std::memset(&p, 0, sizeof(p));
+      p.g = g;
+      p.cstride = g.size();
+      p.v = c->x;
+      p.out = c->tmp;
+      p.E = c->Ek4;
+      return launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
+                                  sweep_shape(g, MODE_APPLY, tw), c->stream);
+    };
+    ST(tune_one(c, std::make_tuple(g.nx, g.ny, 2, (int)SRC_FINE64, c->num_sms), make, &c->tw64));
+  }
+  invalidate_graphs(c);
+  return MTO_OK;
+}
+
+extern "C" {
+
+mto_status mto_get_launch_shape(mto_ctx* c, int level, int* target_warps_out) {
+  if (!c || !target_warps_out || level < 0 || level > c->L) return MTO_ERR_ARG;
+  *target_warps_out = target_warps(c, level);
+  return MTO_OK;
+}
+
+}  // extern "C"

@@ -181,6 +181,12 @@ struct DevScalars {
   int x_nonzero;    // set by the packing of the warm start when any entry is non-zero
 };
 
+// Outcome of one solve, copied from DevScalars at the end of each right-hand side.
+struct RhsStats {
+  int iter, done;
+  double rr, rr_true, ff;
+};
+
 // Finishing actions of the last block of a reduction.
 enum Finish {
   FIN_NONE = 0,

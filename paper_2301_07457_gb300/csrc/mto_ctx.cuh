@@ -1,0 +1,148 @@
+// Internal definition of the libmto context, shared by the translation units
+// that enqueue its work (mto_api.cu: single solves and the C ABI;
+// mto_batch.cu: batched graphs and the launch-shape tuner).
+#pragma once
+
+#include <vector>
+
+#include "mto.h"
+#include "mto_launch.h"
+
+namespace mto {
+
+struct LevelBuf {
+  Grid g{};
+  void* z[2] = {nullptr, nullptr};  // V2<T> vectors (ping-pong)
+  void* b = nullptr;                // right-hand side of this level
+  void* coef = nullptr;             // T coefficients, NCOEF * g.size()
+  void* invd2 = nullptr;            // V2<T> w / D
+  double* mom = nullptr;            // NMOM * g.size() (coarse levels)
+  double* coef64 = nullptr;         // level 0: float64 coefficients for the dense matrix
+};
+
+constexpr int MAX_LEVELS = 16;
+constexpr int MAX_RHS = 64;
+// Launch shapes: warps a sweep exposes, per SM (default and tuner range).
+constexpr int DEFAULT_TARGET_WARPS_PER_SM = 32;
+constexpr int MAX_TARGET_WARPS_PER_SM = 128;
+
+}  // namespace mto
+
+struct mto_ctx {
+  int device = 0, num_sms = 1;
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  // Stream that the enqueue functions use: `stream`, or the stream that
+  // captures the body of the solver's device-side loop.
+  cudaStream_t cs = nullptr, body_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
+  int nelx = 0, nely = 0;
+  double nu = 0.3;
+  unsigned fixed = 0;
+  mto_solver_opts o{};
+  int L = 0;
+  bool mixed = false;
+  std::vector<mto::LevelBuf> lv;
+  // finest level
+  double* E64 = nullptr;
+  double* Ek4 = nullptr;  // E (kA, kB, kC, kG) per element, for the float64 sweeps
+  __nv_bfloat16* Ebf = nullptr;
+  double* invd1 = nullptr;
+  double2 *x = nullptr, *r = nullptr, *q = nullptr, *f = nullptr, *tmp = nullptr;
+  double2* p[2] = {nullptr, nullptr};
+  float2* r32 = nullptr;
+  // coarsest grid
+  int n0 = 0, bw0 = 0;
+  int* dof_index = nullptr;
+  double *Kd = nullptr, *Kinv = nullptr, *invL = nullptr;  // Kd: band storage of K_0 / its factor
+  int* err_flag = nullptr;
+  // reductions
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  mto::DevScalars* sc = nullptr;
+  mto::DevScalars* sc_host = nullptr;  // pinned
+  int* err_host = nullptr;             // pinned
+  mto::RhsStats* rhs_stats = nullptr;       // device [MAX_RHS]
+  mto::RhsStats* rhs_stats_host = nullptr;  // pinned [MAX_RHS]
+  // design
+  bool has_design = false;
+  int n_phase = 0;
+  mto::PhaseTable ph{};
+  double penal = 3.0;
+  int ipenal = 3;
+  double* xdes = nullptr;
+  size_t xdes_cap = 0;
+  // host-call staging (mto_run_host)
+  double *hx = nullptr, *hf = nullptr, *hu = nullptr, *hc = nullptr, *hg = nullptr;
+  size_t hx_cap = 0, hf_cap = 0, hg_cap = 0;
+  int hc_cap = 0;
+  // graph of two PCG iterations (host-polled loop, used when kernel timing is on)
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_kernels = 0;  // kernel nodes in that graph
+  // graph of a whole solve with a device-side loop (conditional while node)
+  cudaGraphExec_t solve_exec = nullptr;
+  long long solve_kernels_fixed = 0;  // kernels outside the loop body
+  long long body_kernels = 0;         // kernels of one loop body (two iterations)
+  long long launches = 0;             // kernels launched by this context (graph nodes included)
+  // launch shapes: target warps of the V-cycle sweeps per level and of the
+  // float64 outer sweeps (K p, residuals) on the finest level (0 = default),
+  // set by the tuner
+  int tw[mto::MAX_LEVELS] = {};
+  int tw64 = 0;
+  // optional event pairs around the hot kernels of each graph iteration:
+  // [parity][0 = outer K p sweep, 1 = first finest-level smoothing sweep][start, end]
+  bool timing = false;
+  bool no_while = false;  // the device-side loop could not be built: host-polled loop
+  cudaEvent_t kev[2][2][2] = {};
+  double ksum[2] = {0.0, 0.0};
+  long long kcnt[2] = {0, 0};
+  int cur_par = -1;
+  // constants
+  mto::FineConst<double> kf64{};
+  mto::FineConst<float> kf32{};
+  double w_over_kdiag = 0.0;
+  // stats
+  float ms_setup = 0.f;
+  mto_solve_stats last{};
+  std::vector<void*> allocs;
+};
+
+namespace mto {
+
+// Last CUDA error that made a call of this thread return MTO_ERR_CUDA.
+extern thread_local cudaError_t g_last_cuda;
+
+#define CK(call)                    \
+  do {                              \
+    cudaError_t e_ = (call);        \
+    if (e_ != cudaSuccess) {        \
+      ::mto::g_last_cuda = e_;      \
+      return MTO_ERR_CUDA;          \
+    }                               \
+  } while (0)
+
+// A kernel launch made by the context: counted, then checked.
+#define KL(call)              \
+  do {                        \
+    c->launches += 1;         \
+    CK(call);                 \
+  } while (0)
+
+#define ST(call)                          \
+  do {                                    \
+    mto_status s_ = (call);               \
+    if (s_ != MTO_OK) return s_;          \
+  } while (0)
+
+// Shared by the translation units (defined in mto_api.cu).
+mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
+                              double penal);
+mto_status enqueue_solve_core(mto_ctx* c);
+mto_status enqueue_rhs_prologue(mto_ctx* c, const double* f_dev, const double* u_dev);
+mto_status enqueue_rhs_epilogue(mto_ctx* c, double* u_dev, int rhs_slot);
+mto_status enqueue_compliance(mto_ctx* c, int n_rhs, const double* f_dev, const double* u_dev,
+                              double* compliance_dev, double* dcdx_dev);
+void invalidate_graphs(mto_ctx* c);
+int target_warps(const mto_ctx* c, int level);
+int target_warps64(const mto_ctx* c);
+
+}  // namespace mto

@@ -55,6 +55,13 @@ cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, cons
                                  const typename V2<T>::t* b, typename V2<T>::t* z,
                                  DevScalars* sc, cudaStream_t s);
 
+// PCG scalars of a fresh solve; loop condition of the device-side solver loop;
+// per-solve outcome record.
+cudaError_t launch_init_scalars(DevScalars* sc, double tol2, int max_it, int flexible, int rr_every,
+                                cudaStream_t s);
+cudaError_t launch_set_continue(cudaGraphConditionalHandle h, const DevScalars* sc, cudaStream_t s);
+cudaError_t launch_record_stats(const DevScalars* sc, RhsStats* dst, cudaStream_t s);
+
 // ---- setup kernels (mto_setup.cu) ----
 struct PhaseTable {
   double E[16];
@@ -84,6 +91,9 @@ cudaError_t launch_coarse_invd(const Grid& g, const T* coef, double omega,
 // Kb[r * (bw + 1) + d] = K_0[r][r - d] (zeroed by the caller).
 cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
                                  int bw, double* Kb, cudaStream_t s);
+// Opt-in shared memory of the coarsest factorisation kernels (once per size,
+// outside any stream capture).
+cudaError_t prepare_cholesky_inverse(int n, int bw);
 // In-place band Cholesky of Kb (1 / L_ii to invL), then the explicit inverse.
 cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
                                     int* err_flag, cudaStream_t s, int num_sms);

@@ -476,44 +476,57 @@ static int max_dyn_smem() {
   return v;
 }
 
+struct CholPlan {
+  size_t pairs, band, win;
+  bool band_smem, inv_smem;
+};
+
+static CholPlan chol_plan(int n, int bw) {
+  CholPlan p;
+  const int W = bw + 1;
+  p.pairs = sizeof(short2) * (size_t)bw * (bw + 1) / 2 + 16;
+  p.band = sizeof(double) * (size_t)n * W;
+  p.win = sizeof(double) * (size_t)W * 32;
+  const int cap = max_dyn_smem();
+  p.band_smem = p.band + p.pairs <= (size_t)cap;
+  p.inv_smem = p.band + p.win <= (size_t)cap;
+  return p;
+}
+
+cudaError_t prepare_cholesky_inverse(int n, int bw) {
+  const CholPlan pl = chol_plan(n, bw);
+  cudaError_t e = cudaSuccess;
+  if (pl.band_smem)
+    e = cudaFuncSetAttribute(cholesky_band_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(pl.band + pl.pairs));
+  else if (pl.pairs > 48 * 1024)
+    e = cudaFuncSetAttribute(cholesky_band_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pl.pairs);
+  if (e != cudaSuccess) return e;
+  if (pl.inv_smem)
+    e = cudaFuncSetAttribute(inverse_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(pl.band + pl.win));
+  else if (pl.win > 48 * 1024)
+    e = cudaFuncSetAttribute(inverse_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pl.win);
+  return e;
+}
+
 cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
                                     int* err_flag, cudaStream_t s, int num_sms) {
   (void)num_sms;
-  const int W = bw + 1;
-  const size_t pairs = sizeof(short2) * (size_t)bw * (bw + 1) / 2 + 16;
-  const size_t band = sizeof(double) * (size_t)n * W;
-  const int cap = max_dyn_smem();
-  cudaError_t e;
-  if (band + pairs <= (size_t)cap) {
-    e = cudaFuncSetAttribute(cholesky_band_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(band + pairs));
-    if (e != cudaSuccess) return e;
-    cholesky_band_kernel<true><<<1, CHOL_NT, band + pairs, s>>>(n, bw, Kb, invL, err_flag);
-  } else {
-    if (pairs > 48 * 1024) {
-      e = cudaFuncSetAttribute(cholesky_band_kernel<false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pairs);
-      if (e != cudaSuccess) return e;
-    }
-    cholesky_band_kernel<false><<<1, CHOL_NT, pairs, s>>>(n, bw, Kb, invL, err_flag);
-  }
-  e = cudaGetLastError();
+  const CholPlan pl = chol_plan(n, bw);
+  if (pl.band_smem)
+    cholesky_band_kernel<true><<<1, CHOL_NT, pl.band + pl.pairs, s>>>(n, bw, Kb, invL, err_flag);
+  else
+    cholesky_band_kernel<false><<<1, CHOL_NT, pl.pairs, s>>>(n, bw, Kb, invL, err_flag);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t win = sizeof(double) * (size_t)W * 32;
   const int blocks = (n + INV_COLS - 1) / INV_COLS;
-  if (band + win <= (size_t)cap) {
-    e = cudaFuncSetAttribute(inverse_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(band + win));
-    if (e != cudaSuccess) return e;
-    inverse_cols_kernel<true><<<blocks, 32, band + win, s>>>(n, bw, Kb, invL, Kinv);
-  } else {
-    if (win > 48 * 1024) {
-      e = cudaFuncSetAttribute(inverse_cols_kernel<false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win);
-      if (e != cudaSuccess) return e;
-    }
-    inverse_cols_kernel<false><<<blocks, 32, win, s>>>(n, bw, Kb, invL, Kinv);
-  }
+  if (pl.inv_smem)
+    inverse_cols_kernel<true><<<blocks, 32, pl.band + pl.win, s>>>(n, bw, Kb, invL, Kinv);
+  else
+    inverse_cols_kernel<false><<<blocks, 32, pl.win, s>>>(n, bw, Kb, invL, Kinv);
   return cudaGetLastError();
 }
 

@@ -213,7 +213,52 @@ __global__ void __launch_bounds__(GEMV_NT)
   if (lane == 0) z[free_idx[row]] = (T)acc;
 }
 
+// PCG scalars of a fresh solve (kernel parameters, so the launch can live in a
+// CUDA graph).
+__global__ void init_scalars_kernel(DevScalars* sc, double tol2, int max_it, int flexible,
+                                    int rr_every) {
+  DevScalars s;
+  memset(&s, 0, sizeof(s));
+  s.tol2 = tol2;
+  s.max_it = max_it;
+  s.flexible = flexible;
+  s.rr_every = rr_every;
+  *sc = s;
+}
+
+// Body condition of the solver's device-side loop: run again while the PCG
+// has not stopped.
+__global__ void set_continue_kernel(cudaGraphConditionalHandle h, const DevScalars* sc) {
+  cudaGraphSetConditional(h, sc->done == RUNNING ? 1u : 0u);
+}
+
+__global__ void record_stats_kernel(const DevScalars* sc, RhsStats* dst) {
+  RhsStats r;
+  r.iter = sc->iter;
+  r.done = sc->done;
+  r.rr = sc->rr;
+  r.rr_true = sc->rr_true;
+  r.ff = sc->ff;
+  *dst = r;
+}
+
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_init_scalars(DevScalars* sc, double tol2, int max_it, int flexible, int rr_every,
+                                cudaStream_t s) {
+  init_scalars_kernel<<<1, 1, 0, s>>>(sc, tol2, max_it, flexible, rr_every);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_continue(cudaGraphConditionalHandle h, const DevScalars* sc, cudaStream_t s) {
+  set_continue_kernel<<<1, 1, 0, s>>>(h, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_record_stats(const DevScalars* sc, RhsStats* dst, cudaStream_t s) {
+  record_stats_kernel<<<1, 1, 0, s>>>(sc, dst);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_jacobi0_fine64(const Grid& g, const double* invd1, const double2* r, double2* z,
                                   DevScalars* sc, int nblocks, cudaStream_t s) {

@@ -17,6 +17,7 @@ from .designs import (  # noqa: F401
     LEFT,
     RIGHT,
     TOP,
+    batch_sizes,
     dirichlet_design,
     load_right_edge,
     load_top_edge,

@@ -58,6 +58,13 @@ def dirichlet_design(nelx, nely, n_phase, seed, chunk=1 << 22):
     return out.reshape(n_phase, nely, nelx)
 
 
+def batch_sizes(n, seed, choices=(128, 256, 512, 1024)):
+    """n square mesh sizes drawn uniformly from `choices` by the counter-based generator."""
+    u = uniform01(seed, np.arange(n, dtype=np.uint64))
+    idx = np.minimum((u * len(choices)).astype(np.int64), len(choices) - 1)
+    return [int(choices[i]) for i in idx]
+
+
 def load_top_edge(nelx, nely, value=-1.0):
     """f_y = value at every top-edge node; layout [nely+1][nelx+1][2]."""
     f = np.zeros((nely + 1, nelx + 1, 2), dtype=np.float64)
