@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--sample-size", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shapes (for profiling)")
     ap.add_argument("--sweep-outer", type=int, default=50)
     return ap.parse_args()
 
@@ -179,6 +180,22 @@ def oracle_sample(n, reps=0, budget=10.0):
 
 def ndof(n):
     return 2 * (n + 1) * (n + 1)
+
+
+def max_over_ranks(v, world, device):
+    """Largest v over the ranks (the slowest rank's time); v itself on one rank."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, ms_max):
+    """Whole-job throughput: every rank solved `steps` problems in at most ms_max."""
+    return world * steps / (ms_max / 1000.0)
 
 
 def cpu_value(d, n_sample, n_full):
@@ -345,12 +362,8 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_here(v):
+        return max_over_ranks(v, world, dev)
 
     def launches(mesh):
         c = ctypes.c_longlong()
@@ -379,7 +392,7 @@ def run_ours(args):
             e1.record()
             torch.cuda.synchronize()
         barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = max_over_ranks_here(e0.elapsed_time(e1))
         return ms, stats, launches(mesh) - l0, clk.summary()
 
     def kernel_times(mesh, steps):
@@ -397,12 +410,12 @@ def run_ours(args):
     common = dict(n_coarsen=nc, tol=1e-8, max_it=1000, device=local)
     mixed = mto.Mesh(n, n, precision="mixed", rr_every=25, flexible=True, **common)
     mixed.set_design(x, EP, PENAL)
-    shapes_mixed = mixed.autotune()
+    shapes_mixed = [mixed.launch_shape(l) for l in range(nc + 1)] if args.no_tune else mixed.autotune()
     ms, stats, nlaunch, clocks = timed(mixed, args.steps, args.warmup)
     kt = kernel_times(mixed, 2)
     iters = [s["iters"] for s in stats]
     solve_ms = [s["ms_solve"] for s in stats]
-    value = world * args.steps / (ms / 1000.0)
+    value = job_value(world, args.steps, ms)
     gdof = ndof(n) * sum(iters) / (ms / 1000.0) / 1e9
     gdof_solve = ndof(n) * sum(iters) / (sum(solve_ms) / 1000.0) / 1e9
 
@@ -425,11 +438,12 @@ def run_ours(args):
     if args.fp64_steps > 0:
         m64 = mto.Mesh(n, n, precision="fp64", **common)
         m64.set_design(x, EP, PENAL)
-        m64.autotune()
+        if not args.no_tune:
+            m64.autotune()
         ms64, st64, _, clk64 = timed(m64, args.fp64_steps, 1)
         kt64 = kernel_times(m64, 1)
         it64 = [s["iters"] for s in st64]
-        v64 = world * args.fp64_steps / (ms64 / 1000.0)
+        v64 = job_value(world, args.fp64_steps, ms64)
         fp64 = {"solves_s": v64, "ms_per_step": ms64 / args.fp64_steps, "iters": it64,
                 "gdof_iter_s": ndof(n) * sum(it64) / (ms64 / 1000.0) / 1e9,
                 "rel_res_true": max(s["rel_res_true"] for s in st64),
@@ -470,7 +484,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             host_step()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks_here(time.perf_counter() - t0)
         e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": xh.numel() * 8 + fh.numel() * 8,
                "d2h_bytes_per_step": uh.numel() * 8 + gh.numel() * 8 + 8}

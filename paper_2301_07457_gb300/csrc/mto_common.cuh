@@ -62,6 +62,22 @@ template <typename T> struct V2;
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<float> { using t = float2; };
 
+// Exact float -> double conversion on the integer pipe: normal numbers,
+// zeros, infinities and NaNs keep their value; float subnormals (below 1.2e-38)
+// become signed zero.  On GB300 the FP64 pipe (two operations per clock per
+// SM) would also execute a hardware conversion, so kernels bound by that
+// pipe convert here instead.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
+  const unsigned hi = (b & 0x80000000u) | (e ? ((ed << 20) | ((b >> 3) & 0xfffffu)) : 0u);
+  const unsigned lo = e ? (b << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double to_f64(float f) { return f2d_exact(f); }
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 template <typename T> __device__ __forceinline__ typename V2<T>::t mk2(T x, T y) {
   typename V2<T>::t r;
   r.x = x;

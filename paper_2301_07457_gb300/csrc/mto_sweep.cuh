@@ -184,7 +184,11 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
   __device__ __forceinline__ static T2 finish_v(const SweepParams<T>& a, const VR& r, int ii, int jj,
                                                 T beta) {
     if constexpr (MODE == MODE_KP) {
-      return mk2<T>(T(r.z.x) + beta * r.v.x, T(r.z.y) + beta * r.v.y);
+      if constexpr (sizeof(T) == 8) {
+        return mk2<T>(to_f64(r.z.x) + beta * r.v.x, to_f64(r.z.y) + beta * r.v.y);
+      } else {
+        return mk2<T>(T(r.z.x) + beta * r.v.x, T(r.z.y) + beta * r.v.y);
+      }
     } else if constexpr (MODE == MODE_PSMOOTH) {
       if (!a.g.valid(ii, jj)) return mk2<T>(T(0), T(0));
       const T wx0 = (ii & 1) ? T(0.5) : T(1), wx1 = (ii & 1) ? T(0.5) : T(0);
@@ -446,8 +450,9 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
           if (inb) a.out[k] = zn;
           if constexpr (DOT) {
             if (act) {
-              dot0 += double(zn.x) * cur.n.rd.x + double(zn.y) * cur.n.rd.y;
-              if (a.qdot != nullptr) dot1 += double(zn.x) * cur.n.qd.x + double(zn.y) * cur.n.qd.y;
+              const double zx = to_f64(zn.x), zy = to_f64(zn.y);
+              dot0 += zx * cur.n.rd.x + zy * cur.n.rd.y;
+              if (a.qdot != nullptr) dot1 += zx * cur.n.qd.x + zy * cur.n.qd.y;
             }
           }
         } else if constexpr (MODE == MODE_RESTRICT) {

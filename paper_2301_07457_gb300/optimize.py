@@ -20,8 +20,8 @@ steps below are this library's reading of it:
     with lam found by bisection (on the device) so that the phase-a volume
     equals V_a; then x_b = s - x_a.
 
-The solve and the sensitivities run in libmto; the filter and the OC step are
-elementwise/convolution tensor operations on the device.  Checkpoints hold the
+The solve and the sensitivities run in libmto; the filter (float32) and the
+OC step are elementwise/convolution tensor operations on the device.  Checkpoints hold the
 design, the displacement (the next warm start), the iteration counter and the
 history.
 """
@@ -43,11 +43,16 @@ def filter_kernel(rf, device, dtype=torch.float64):
 
 
 def filter_sensitivity(d, x, H):
-    """Distance-weighted sensitivity filter (see module docstring); d, x: [nely][nelx]."""
+    """Distance-weighted sensitivity filter (see module docstring); d, x: [nely][nelx].
+
+    The filter is a smoothing heuristic of the optimiser, so it runs in float32
+    (the result is returned in d's dtype).
+    """
     pad = H.shape[-1] // 2
-    num = F.conv2d((x * d)[None, None], H, padding=pad)[0, 0]
-    den = F.conv2d(torch.ones_like(x)[None, None], H, padding=pad)[0, 0]
-    return num / (torch.clamp(x, min=1e-3) * den)
+    H32 = H.to(torch.float32)
+    num = F.conv2d((x * d).to(torch.float32)[None, None], H32, padding=pad)[0, 0]
+    den = F.conv2d(torch.ones_like(x, dtype=torch.float32)[None, None], H32, padding=pad)[0, 0]
+    return (num / (torch.clamp(x.to(torch.float32), min=1e-3) * den)).to(d.dtype)
 
 
 def oc_update(xa, s, d, target, move=0.2, eta=0.5, eps=1e-3, iters=80):

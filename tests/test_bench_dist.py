@@ -1,0 +1,69 @@
+"""Multi-rank host logic of bench.py on CPU ranks (gloo, world size 2).
+
+Every rank solves its own problems (no collective on the data path); only
+the timing is reduced: the job's time is the slowest rank's, and the value
+counts every rank's solves.
+"""
+
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms_local = 100.0 + 50.0 * rank  # rank 1 is slower
+    ms = bench.max_over_ranks(ms_local, world, "cpu")
+    out[rank] = (ms, bench.job_value(world, 5, ms))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time():
+    port = free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    assert out[0] == out[1]
+    ms, value = out[0]
+    assert ms == 150.0
+    assert value == pytest.approx(2 * 5 / 0.150)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
+    assert bench.job_value(1, 4, 2000.0) == 2.0
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+
+    class Args:
+        size, sample_size, warmup, steps, gpus = 2048, 512, 3, 5, 2
+
+    called = []
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1))
+    assert bench.run_reference(Args()) == 0
+    assert not called

@@ -1,0 +1,137 @@
+"""Edge cases of the C ABI on the GPU: degenerate meshes, constraints,
+statuses.  Every case is checked against the oracle or against the status the
+header promises."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fem, solver
+from synth import BOTTOM, LEFT, RIGHT, TOP, dirichlet_design, load_right_edge, load_top_edge
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+EP = [1.0, 0.5, 0.25, 1e-9]
+
+
+@pytest.fixture(scope="module")
+def mto():
+    import paper_2301_07457_gb300 as m
+    return m
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+@pytest.mark.parametrize("nelx,nely,nc", [(2, 2, 1), (4, 2, 1), (8, 2, 1), (2, 8, 1), (6, 10, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tiny_meshes(mto, nelx, nely, nc, prec):
+    x = dirichlet_design(nelx, nely, 4, seed=nelx * 10 + nely)
+    f = load_top_edge(nelx, nely) + load_right_edge(nelx, nely)
+    m = mto.Mesh(nelx, nely, n_coarsen=nc, precision=prec, tol=1e-10 if prec == "fp64" else 1e-8)
+    m.set_design(to_dev(x), EP, 3.0)
+    u, st = m.solve(to_dev(f))
+    ud = solver.solve_direct(nelx, nely, x, EP, 3.0, f)
+    assert rel(u.cpu().numpy(), ud) < (1e-8 if prec == "fp64" else 1e-5)
+    m.close()
+
+
+@pytest.mark.parametrize("fixed", [BOTTOM, LEFT, RIGHT, TOP, BOTTOM | TOP, LEFT | RIGHT,
+                                   BOTTOM | LEFT | RIGHT | TOP])
+def test_every_clamped_edge_pattern(mto, fixed):
+    nelx, nely = 40, 24
+    x = dirichlet_design(nelx, nely, 4, seed=fixed)
+    f = np.random.default_rng(fixed).standard_normal((nely + 1, nelx + 1, 2))
+    m = mto.Mesh(nelx, nely, fixed_edges=fixed, n_coarsen=2, tol=1e-10)
+    m.set_design(to_dev(x), EP, 3.0)
+    u, st = m.solve(to_dev(f))
+    ud = solver.solve_direct(nelx, nely, x, EP, 3.0, f, fixed_edges=fixed)
+    assert rel(u.cpu().numpy(), ud) < 1e-8
+    un = u.cpu().numpy()
+    assert np.all(un[fem.fixed_node_mask(nelx, nely, fixed)] == 0.0)
+    m.close()
+
+
+def test_material_law_variants(mto):
+    nelx, nely = 32, 32
+    for n_phase, Ep, penal, nu in [(1, [1.0], 3.0, 0.3), (4, EP, 2.5, 0.3), (4, EP, 3.0, 0.25),
+                                   (2, [2.0, 0.1], 1.0, 0.45)]:
+        x = dirichlet_design(nelx, nely, n_phase, seed=n_phase)
+        f = load_top_edge(nelx, nely)
+        m = mto.Mesh(nelx, nely, nu=nu, n_coarsen=2, tol=1e-10)
+        m.set_design(to_dev(x), Ep, penal)
+        u, _ = m.solve(to_dev(f))
+        C, g = m.compliance_grad(to_dev(f), u)
+        ud = solver.solve_direct(nelx, nely, x, Ep, penal, f, nu=nu)
+        C_ref, g_ref = solver.compliance_and_gradient(nelx, nely, x, Ep, penal, f, ud, nu=nu)
+        assert rel(u.cpu().numpy(), ud) < 1e-8
+        assert abs(C.item() - C_ref) / C_ref < 1e-9
+        assert np.abs(g.cpu().numpy() - g_ref).max() <= 1e-7 * np.abs(g_ref).max()
+        m.close()
+
+
+def test_statuses(mto):
+    from paper_2301_07457_gb300 import MtoError, _lib
+    nelx = nely = 32
+    x = to_dev(dirichlet_design(nelx, nely, 4, seed=1))
+    f = to_dev(load_top_edge(nelx, nely))
+    m = mto.Mesh(nelx, nely, n_coarsen=2, tol=1e-12, max_it=3)
+    with pytest.raises(MtoError) as e:
+        m.solve(f)
+    assert e.value.code == _lib.ERR_STATE  # solve before set_design
+    m.set_design(x, EP, 3.0)
+    u, st = m.solve(f, raise_on_failure=False)
+    assert st["status"] == "MTO_ERR_NOT_CONVERGED" and st["iters"] == 3
+    assert torch.isfinite(u).all() and u.abs().max() > 0
+    # Zero load: converged at once with u = 0.
+    u0, st0 = m.solve(torch.zeros_like(f))
+    assert st0["iters"] == 0 and st0["converged"] == 1 and u0.abs().max().item() == 0.0
+    # A NaN in the design cannot be factorised: breakdown, not a fault.
+    xb = x.clone()
+    xb[0, 5, 5] = float("nan")
+    with pytest.raises(MtoError) as e2:
+        m.set_design(xb, EP, 3.0)
+    assert e2.value.code == _lib.ERR_BREAKDOWN
+    # The context stays usable.
+    m.set_design(x, EP, 3.0)
+    u2, st2 = m.solve(f, raise_on_failure=False)
+    assert st2["iters"] == 3
+    m.close()
+
+
+def test_mesh_limits(mto):
+    from paper_2301_07457_gb300 import MtoError, _lib
+    with pytest.raises(MtoError) as e:
+        mto.Mesh(128, 128, n_coarsen=1)  # coarsest 64 x 64: 8320 free DOFs > 4096
+    assert e.value.code == _lib.ERR_UNSUPPORTED_MESH
+    with pytest.raises(MtoError) as e:
+        mto.Mesh(100, 64, n_coarsen=3)
+    assert e.value.code == _lib.ERR_UNSUPPORTED_MESH
+    m = mto.Mesh(64, 64, n_coarsen=1)  # coarsest 32 x 32: 2112 free DOFs, band Cholesky in global memory
+    x = dirichlet_design(64, 64, 4, seed=9)
+    f = load_top_edge(64, 64)
+    m.set_design(to_dev(x), EP, 3.0)
+    u, st = m.solve(to_dev(f))
+    assert rel(u.cpu().numpy(), solver.solve_direct(64, 64, x, EP, 3.0, f)) < 1e-7
+    assert m.info()["coarsest_free_dofs"] == 2112
+    m.close()
+
+
+def test_mixed_rediscretised_and_partial_warm_start(mto):
+    nelx, nely = 128, 128
+    x = dirichlet_design(nelx, nely, 4, seed=12)
+    f = load_top_edge(nelx, nely)
+    E = fem.simp_moduli(x, EP, 3.0)
+    m = mto.Mesh(nelx, nely, n_coarsen=3, precision="mixed", coarse_kind="rediscretize", tol=1e-8)
+    m.set_design(to_dev(x), EP, 3.0)
+    u, st = m.solve(to_dev(f))
+    assert solver.true_relative_residual(nelx, nely, E, f, u.cpu().numpy()) <= 1e-8
+    u_half, st_half = m.solve(to_dev(f), u0=0.5 * u)
+    assert st_half["iters"] <= st["iters"]
+    assert solver.true_relative_residual(nelx, nely, E, f, u_half.cpu().numpy()) <= 1e-8
+    m.close()
