@@ -132,7 +132,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     p.coef = (const T*)L.coef;
     p.invd2 = (const T2*)L.invd2;
     if (cfine) set_cfine(c, p);
-    return launch_sweep<T>(src, mode, false, false, p, sweep_shape(L.g, mode, tw), c->cs);
+    return launch_sweep<T>(src, mode, false, false, p, tw, c->cs);
   };
   // Pre-smoothing from U = 0: the first sweep (U = w D^-1 F) is formed on the
   // fly inside the second when there are two or more.
@@ -176,17 +176,18 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   const int tw = target_warps(c, c->L);
   const int nb = vec_blocks(L.g.size(), c->num_sms);
   const int src = MIX ? SRC_FINEBF : SRC_FINE64;
-  const T2* b;
-  // float64: the first pre-sweep from zero is fused into the second (SMOOTH0).
-  // mixed: the pointwise first sweep also writes the float32 copy of r.
-  const bool fused0 = !MIX && c->o.nu1 >= 2;
-  if constexpr (MIX) {
-    KL(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r, c->r32, (float2*)L.z[0], sc,
-                             nb, c->cs));
-    b = (const T2*)c->r32;
-  } else {
-    if (!fused0) KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->cs));
-    b = (const T2*)c->r;
+  // The first pre-sweep from zero is fused into the second (SMOOTH0) when
+  // there are two or more.  The mixed cycle reads the float32 copy of r that
+  // the kernels writing r (CG update, residuals) keep next to it.
+  const T2* b = MIX ? (const T2*)c->r32 : (const T2*)c->r;
+  const bool fused0 = c->o.nu1 >= 2;
+  if (!fused0) {
+    if constexpr (MIX) {
+      KL(launch_jacobi0_finebf(L.g, c->Ebf, (float)c->w_over_kdiag, c->r32, (float2*)L.z[0], sc, nb,
+                               c->cs));
+    } else {
+      KL(launch_jacobi0_fine64(L.g, c->invd1, c->r, (double2*)L.z[0], sc, nb, c->cs));
+    }
   }
   int cur = 0;
   auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc, bool dot) -> cudaError_t {
@@ -208,7 +209,7 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
       p.qdot = c->o.flexible ? c->q : nullptr;
       p.finish = FIN_RHO;
     }
-    return launch_sweep<T>(src, mode, dot, false, p, sweep_shape(L.g, mode, tw), c->cs);
+    return launch_sweep<T>(src, mode, dot, false, p, tw, c->cs);
   };
   // Timing events bracket the first finest-level smoothing kernel.
   const bool tm = c->timing && sc != nullptr && c->cur_par >= 0;
@@ -267,8 +268,9 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.out = out;
   p.E = c->Ek4;
   p.finish = finish;
+  if (c->mixed && out == c->r) p.out32 = c->r32;
   KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
-                          sweep_shape(g, MODE_RESID, target_warps64(c)), c->cs));
+                          target_warps64(c), c->cs));
   return MTO_OK;
 }
 
@@ -297,10 +299,11 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.E = c->Ek4;
     p.finish = FIN_PQ;
     KL(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
-                            sweep_shape(g, MODE_KP, target_warps64(c)), c->cs));
+                            target_warps64(c), c->cs));
   }
   if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->cs, cudaEventRecordExternal));
-  KL(launch_update(g, c->x, c->r, c->p[par ^ 1], c->q, c->partials, c->ticket, c->sc,
+  KL(launch_update(g, c->x, c->r, c->mixed ? c->r32 : nullptr, c->p[par ^ 1], c->q, c->partials,
+                   c->ticket, c->sc,
                    vec_blocks(g.size(), c->num_sms), c->cs));
   if (c->mixed && c->o.rr_every > 0) ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1));
   return MTO_OK;
@@ -813,8 +816,10 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   // Reduction scratch: two partials per block of the largest launch.
   int maxb = vec_blocks(gf.size(), c->num_sms);
   for (int mode = 0; mode <= MODE_RESTRICT; ++mode) {
-    const SweepShape s = sweep_shape(gf, mode, MAX_TARGET_WARPS_PER_SM * c->num_sms);
-    if (s.nblocks > maxb) maxb = s.nblocks;
+    for (int cols = 1; cols <= 2; ++cols) {
+      const SweepShape s = sweep_shape(gf, mode, MAX_TARGET_WARPS_PER_SM * c->num_sms, cols);
+      if (s.nblocks > maxb) maxb = s.nblocks;
+    }
   }
   ST(dalloc_t(c, &c->partials, 2 * (size_t)maxb + 2));
   ST(dalloc_t(c, &c->ticket, 4));
@@ -951,7 +956,7 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     p.out = c->q;
     p.E = c->Ek4;
     KL(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
-                            sweep_shape(B.g, MODE_APPLY, tw), c->cs));
+                            tw, c->cs));
     KL(launch_unpack(B.g, c->q, y_dev, c->cs, c->num_sms));
   } else if (c->mixed) {
     KL(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->cs, c->num_sms));
@@ -964,7 +969,7 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     const bool cfine = level == c->L - 1;
     if (cfine) set_cfine(c, p);
     KL(launch_sweep<float>(fine ? SRC_FINEBF : (cfine ? SRC_CFINE : SRC_COARSE), MODE_APPLY, false,
-                           false, p, sweep_shape(B.g, MODE_APPLY, tw), c->cs));
+                           false, p, tw, c->cs));
     KL(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->cs, c->num_sms));
   } else {
     KL(launch_pack(B.g, v_dev, (double2*)B.z[0], c->cs, c->num_sms));
@@ -973,7 +978,7 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     p.out = (double2*)B.z[1];
     p.coef = (const double*)B.coef;
     KL(launch_sweep<double>(SRC_COARSE, MODE_APPLY, false, false, p,
-                            sweep_shape(B.g, MODE_APPLY, tw), c->cs));
+                            tw, c->cs));
     KL(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->cs, c->num_sms));
   }
   return leave(c);
@@ -987,6 +992,7 @@ mto_status mto_apply_preconditioner(mto_ctx* c, const double* r_dev, double* z_d
   KL(launch_pack(B.g, r_dev, c->r, c->cs, c->num_sms));
   int zi = 0;
   if (c->mixed) {
+    KL(launch_pack_f32(B.g, r_dev, c->r32, c->cs, c->num_sms));
     ST(fine_cycle<float>(c, nullptr, false, &zi));
     KL(launch_unpack_f32(B.g, (const float2*)B.z[zi], z_dev, c->cs, c->num_sms));
   } else {

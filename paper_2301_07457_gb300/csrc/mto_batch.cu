@@ -333,8 +333,7 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
           p.gfine = c->lv[c->L].g;
           p.redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
         }
-        return launch_sweep<float>(src, MODE_SMOOTH, false, false, p, sweep_shape(B.g, MODE_SMOOTH, tw),
-                                   c->stream);
+        return launch_sweep<float>(src, MODE_SMOOTH, false, false, p, tw, c->stream);
       }
       SweepParams<double> p;
       std::memset(&p, 0, sizeof(p));
@@ -347,8 +346,7 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
       p.invd1 = c->invd1;
       p.coef = (const double*)B.coef;
       p.invd2 = (const double2*)B.invd2;
-      return launch_sweep<double>(src, MODE_SMOOTH, false, false, p, sweep_shape(B.g, MODE_SMOOTH, tw),
-                                  c->stream);
+      return launch_sweep<double>(src, MODE_SMOOTH, false, false, p, tw, c->stream);
     };
     ST(tune_one(c, std::make_tuple(B.g.nx, B.g.ny, (int)f32, src, c->num_sms), make, &c->tw[l]));
   }
@@ -365,7 +363,7 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
       p.out = c->tmp;
       p.E = c->Ek4;
       return launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
-                                  sweep_shape(g, MODE_APPLY, tw), c->stream);
+                                  tw, c->stream);
     };
     ST(tune_one(c, std::make_tuple(g.nx, g.ny, 2, (int)SRC_FINE64, c->num_sms), make, &c->tw64));
   }

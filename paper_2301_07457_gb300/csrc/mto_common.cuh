@@ -51,29 +51,100 @@ inline Grid make_grid(int nx, int ny, unsigned fixed) {
   Grid g;
   g.nx = nx;
   g.ny = ny;
-  // Lanes of the marching sweeps read up to column nx + 32.
-  g.pitch = ((OFFX + nx + 34) + 31) / 32 * 32;
+  // Lanes of the marching sweeps read up to column nx + 62 (two columns per
+  // lane) and down to column -2.
+  g.pitch = ((OFFX + nx + 66) + 31) / 32 * 32;
   g.rows = ny + 4;
   g.fixed = fixed;
   return g;
+}
+
+// Programmatic dependent launch.  The kernels of the PCG iteration are
+// launched with launch_pdl (mto_launch.h): the next kernel on the stream may
+// be scheduled while this one runs, and each of them calls pdl_wait() before
+// its first global memory access, which returns once the previous grid has
+// completed and its writes are visible.  The early trigger lets the next
+// kernel's blocks take SM slots as this kernel's blocks retire, which hides
+// the launch latency between the many short kernels of a V-cycle.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;" ::: "memory");
 }
 
 template <typename T> struct V2;
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<float> { using t = float2; };
 
-// Exact float -> double conversion on the integer pipe: normal numbers,
-// zeros, infinities and NaNs keep their value; float subnormals (below 1.2e-38)
-// become signed zero.  On GB300 the FP64 pipe (two operations per clock per
-// SM) would also execute a hardware conversion, so kernels bound by that
-// pipe convert here instead.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned b = __float_as_uint(f);
+// Bit casts usable on the host (tests) and the device.
+__host__ __device__ __forceinline__ unsigned long long bits_of(double d) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(d);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &d, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  __builtin_memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned bits_of(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned b;
+  __builtin_memcpy(&b, &f, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  __builtin_memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
+
+// Conversions between float and double on the integer pipe.  On GB300 the
+// FP64 pipe (two operations per clock per SM) also executes the hardware
+// conversions, so kernels that are bound by that pipe, or that would become
+// bound by it, convert here instead.
+//
+// f2d_exact: exact; normal numbers, zeros, infinities and NaNs keep their
+// value; float subnormals (below 1.2e-38) become signed zero.
+__host__ __device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = bits_of(f);
   const unsigned e = (b >> 23) & 0xffu;
   const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
   const unsigned hi = (b & 0x80000000u) | (e ? ((ed << 20) | ((b >> 3) & 0xfffffu)) : 0u);
   const unsigned lo = e ? (b << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
+  return double_of(((unsigned long long)hi << 32) | lo);
+}
+// d2f_rn: IEEE 754 round-to-nearest-even of the 52-bit significand to 23
+// bits (ties to even).  Results below the float normal range (1.18e-38)
+// become signed zero, overflow gives infinity, NaN stays NaN.
+__host__ __device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long b = bits_of(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int fe = e - 896;                                  // rebias 1023 -> 127
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // leading 23 significand bits
+  const unsigned half = (lo >> 28) & 1u;                   // first dropped bit
+  const unsigned rest = lo & 0x0fffffffu;                  // the other dropped bits
+  unsigned r = ((unsigned)fe << 23) + m;
+  r += half & ((rest != 0u ? 1u : 0u) | (m & 1u));  // a carry moves into the exponent
+  if (fe <= 0) r = 0u;
+  if (fe >= 255) r = 0x7f800000u;
+  if (e == 0x7ff) r = ((hi & 0xfffffu) | lo) != 0u ? 0x7fc00000u : 0x7f800000u;
+  return float_of(sign | r);
 }
 __device__ __forceinline__ double to_f64(float f) { return f2d_exact(f); }
 __device__ __forceinline__ double to_f64(double d) { return d; }

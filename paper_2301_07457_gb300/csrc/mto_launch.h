@@ -2,20 +2,59 @@
 // float64 sweeps, the float32 sweeps, the setup and the vector kernels).
 #pragma once
 
-#include "mto_sweep.cuh"
+#include <utility>
+
+#include "mto_sweep2.cuh"
 
 namespace mto {
 
-// Launch shape of a sweep over grid g (see mto_sweep.cuh).  target_warps is
-// the number of warps the launch should expose (a multiple of the SM count).
+// Launch a kernel that calls pdl_wait() first, allowing programmatic
+// dependent launch after the previous kernel on the stream (captured into
+// graphs as a programmatic edge).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Launch shape of a sweep over grid g (see mto_sweep.cuh and mto_sweep2.cuh).
+// target_warps is the number of warps the launch should expose (a multiple of
+// the SM count); cols is the number of node columns per lane (1 or 2).
 struct SweepShape {
   int nstrips, nchunks, H, nblocks;
 };
-SweepShape sweep_shape(const Grid& g, int mode, int target_warps);
+SweepShape sweep_shape(const Grid& g, int mode, int target_warps, int cols);
 
+// Node columns per lane of the instantiation that launch_sweep uses for a
+// float64 (f64) or float32 sweep of source src in mode `mode`.  Two for the
+// float32 sweeps of the finest and first coarse level (issue-bound) and for
+// the float64 outer operator sweeps (K p, residuals: 3% less halo work on
+// the FP64 pipe); one for the float64 V-cycle and for levels with 13 stored
+// coefficients per element, where a pair of elements needs too many
+// registers.
+constexpr int sweep_cols_of(bool f64, int src, int mode) {
+  if (f64) {
+    return (src == SRC_FINE64 && (mode == MODE_KP || mode == MODE_RESID || mode == MODE_APPLY)) ? 2 : 1;
+  }
+  return src == SRC_COARSE ? 1 : 2;
+}
+int sweep_cols(bool f64, int src, int mode);
+
+// Launch one sweep over p.g; the launch shape follows from target_warps.
 template <typename T>
 cudaError_t launch_sweep(int src, int mode, bool dot, bool zfloat, SweepParams<T> p,
-                         const SweepShape& sh, cudaStream_t s);
+                         int target_warps, cudaStream_t s);
 
 // ---- pointwise kernels (mto_vec.cu) ----
 constexpr int VEC_NT = 256;
@@ -24,18 +63,19 @@ int vec_blocks(long long n, int num_sms);
 // z = invd1 (.) r on the float64 finest level.
 cudaError_t launch_jacobi0_fine64(const Grid& g, const double* invd1, const double2* r, double2* z,
                                   DevScalars* sc, int nblocks, cudaStream_t s);
-// r32 = float(r); z = w / (KE_00 sum E) (.) r32 on the float32 finest level.
+// z = w / (KE_00 sum E) (.) r32 on the float32 finest level.
 cudaError_t launch_jacobi0_finebf(const Grid& g, const __nv_bfloat16* E, float wdiag,
-                                  const double2* r, float2* r32, float2* z, DevScalars* sc,
-                                  int nblocks, cudaStream_t s);
+                                  const float2* r32, float2* z, DevScalars* sc, int nblocks,
+                                  cudaStream_t s);
 template <typename T>
 cudaError_t launch_jacobi0_coarse(const Grid& g, const typename V2<T>::t* invd2,
                                   const typename V2<T>::t* b, typename V2<T>::t* z,
                                   DevScalars* sc, int nblocks, cudaStream_t s);
 // x += alpha p; r -= alpha q; rr = |r|^2 (FIN_UPDATE).
-cudaError_t launch_update(const Grid& g, double2* x, double2* r, const double2* p, const double2* q,
-                          double* partials, unsigned* ticket, DevScalars* sc, int nblocks,
-                          cudaStream_t s);
+// x += alpha p, r -= alpha q, rr = |r|^2 (FIN_UPDATE); r32 = float(r) when not null.
+cudaError_t launch_update(const Grid& g, double2* x, double2* r, float2* r32, const double2* p,
+                          const double2* q, double* partials, unsigned* ticket, DevScalars* sc,
+                          int nblocks, cudaStream_t s);
 // sum a.b over n double2 values (finish kind applied to sc, result also to out_value).
 cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* partials,
                        unsigned* ticket, DevScalars* sc, int finish, double* out_value,

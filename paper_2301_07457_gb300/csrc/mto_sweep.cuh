@@ -74,6 +74,7 @@ template <typename T> struct SweepParams {
   T2* p_out;         // KP: new search direction
   const T2* b;       // right-hand side (SMOOTH, SMOOTH0, PSMOOTH, RESTRICT, RESID)
   T2* out;           // output vector (APPLY, RESID, KP: q, SMOOTH*, PSMOOTH)
+  float2* out32;     // RESID: optional float32 copy of out (the mixed V-cycle's input)
   T2* bc;            // RESTRICT: coarse right-hand side
   const void* E;     // finest level: 4 scaled float64 moduli per element (FINE64) or bf16 E
   const T* coef;     // coarse element matrices, NCOEF arrays of g.size()
@@ -295,7 +296,11 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
   using S = Sweep<T, SRC, MODE, DOT, ZT>;
   using VR = typename S::VR;
   using ER = typename S::ER;
+  // The bf16 finest level stores no w/D; its fused first sweep exists only
+  // in the two-column kernel (mto_sweep2.cuh).
+  static_assert(!(SRC == SRC_FINEBF && MODE == MODE_SMOOTH0), "use sweep2_kernel");
   constexpr bool REDUCE = DOT || MODE == MODE_RESID || MODE == MODE_KP;
+  pdl_wait();
   if (a.sc != nullptr && a.gate) {
     if (a.sc->done != RUNNING) return;  // uniform over the grid
     if (a.replace_gate && (a.sc->rr_every <= 0 || (a.sc->iter % a.sc->rr_every) != 0)) return;
@@ -322,7 +327,8 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
         T2 r = mk2<T>(T(0), T(0));
         if (!g.is_fixed(i, j)) r = a.b[k];
         a.out[k] = r;
-        dot0 += double(r.x) * double(r.x) + double(r.y) * double(r.y);
+        if (a.out32 != nullptr) a.out32[k] = make_float2(float(r.x), float(r.y));
+        dot0 = fma(double(r.x), double(r.x), fma(double(r.y), double(r.y), dot0));
       }
     }
   } else if (chunk < a.nchunks) {
@@ -424,14 +430,15 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
           T2 r = mk2<T>(T(0), T(0));
           if (act) r = sub2(cur.n.b, kv);
           if (inb) a.out[k] = r;
-          dot0 += double(r.x) * double(r.x) + double(r.y) * double(r.y);
+          if (inb && a.out32 != nullptr) a.out32[k] = make_float2(float(r.x), float(r.y));
+          dot0 = fma(double(r.x), double(r.x), fma(double(r.y), double(r.y), dot0));
         } else if constexpr (MODE == MODE_KP) {
           const T2 q = act ? kv : mk2<T>(T(0), T(0));
           if (inb) {
             a.p_out[k] = vb;
             a.out[k] = q;
           }
-          if (inb) dot0 += double(vb.x) * double(q.x) + double(vb.y) * double(q.y);
+          if (inb) dot0 = fma(double(vb.x), double(q.x), fma(double(vb.y), double(q.y), dot0));
         } else if constexpr (S::SMOOTHING) {
           T2 zn = mk2<T>(T(0), T(0));
           if (act) {
@@ -451,8 +458,8 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep_kernel(const SweepParams<T> a)
           if constexpr (DOT) {
             if (act) {
               const double zx = to_f64(zn.x), zy = to_f64(zn.y);
-              dot0 += zx * cur.n.rd.x + zy * cur.n.rd.y;
-              if (a.qdot != nullptr) dot1 += zx * cur.n.qd.x + zy * cur.n.qd.y;
+              dot0 = fma(zx, cur.n.rd.x, fma(zy, cur.n.rd.y, dot0));
+              if (a.qdot != nullptr) dot1 = fma(zx, cur.n.qd.x, fma(zy, cur.n.qd.y, dot1));
             }
           }
         } else if constexpr (MODE == MODE_RESTRICT) {

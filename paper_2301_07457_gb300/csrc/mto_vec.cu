@@ -24,6 +24,7 @@ __device__ __forceinline__ bool stop_now(const DevScalars* sc) {
 __global__ void jacobi0_fine64_kernel(Grid g, const double* __restrict__ invd1,
                                       const double2* __restrict__ r, double2* __restrict__ z,
                                       const DevScalars* sc) {
+  pdl_wait();
   if (stop_now(sc)) return;
   const long long n = g.size();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -41,24 +42,23 @@ __global__ void jacobi0_fine64_kernel(Grid g, const double* __restrict__ invd1,
 }
 
 __global__ void jacobi0_finebf_kernel(Grid g, const __nv_bfloat16* __restrict__ E, float wdiag,
-                                      const double2* __restrict__ r, float2* __restrict__ r32,
-                                      float2* __restrict__ z, const DevScalars* sc) {
+                                      const float2* __restrict__ r32, float2* __restrict__ z,
+                                      const DevScalars* sc) {
+  pdl_wait();
   if (stop_now(sc)) return;
   const long long n = g.size();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     int i, j;
     node_of(g, k, i, j);
-    const double2 rr = r[k];
-    const float2 rf = make_float2((float)rr.x, (float)rr.y);
     float2 out = make_float2(0.f, 0.f);
     if (g.active(i, j)) {
+      const float2 rf = r32[k];
       const float se = __bfloat162float(E[k]) + __bfloat162float(E[k - 1]) +
                        __bfloat162float(E[k - g.pitch]) + __bfloat162float(E[k - g.pitch - 1]);
-      const float d = wdiag / se;
+      const float d = __fdividef(wdiag, se);
       out = make_float2(d * rf.x, d * rf.y);
     }
-    r32[k] = rf;
     z[k] = out;
   }
 }
@@ -67,6 +67,7 @@ template <typename T>
 __global__ void jacobi0_coarse_kernel(Grid g, const typename V2<T>::t* __restrict__ invd2,
                                       const typename V2<T>::t* __restrict__ b,
                                       typename V2<T>::t* __restrict__ z, const DevScalars* sc) {
+  pdl_wait();
   if (stop_now(sc)) return;
   const long long n = g.size();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -84,8 +85,10 @@ __global__ void jacobi0_coarse_kernel(Grid g, const typename V2<T>::t* __restric
 
 __global__ void __launch_bounds__(VEC_NT)
     update_kernel(long long n, double2* __restrict__ x, double2* __restrict__ r,
-                  const double2* __restrict__ p, const double2* __restrict__ q, double* partials,
-                  unsigned* ticket, DevScalars* sc) {
+                  float2* __restrict__ r32, const double2* __restrict__ p,
+                  const double2* __restrict__ q, double* partials, unsigned* ticket,
+                  DevScalars* sc) {
+  pdl_wait();
   if (sc->done != RUNNING) return;
   const double alpha = sc->alpha;
   double acc = 0.0;
@@ -99,7 +102,8 @@ __global__ void __launch_bounds__(VEC_NT)
     rr.y -= alpha * qq.y;
     x[k] = xx;
     r[k] = rr;
-    acc += rr.x * rr.x + rr.y * rr.y;
+    if (r32 != nullptr) r32[k] = make_float2(d2f_rn(rr.x), d2f_rn(rr.y));
+    acc = fma(rr.x, rr.x, fma(rr.y, rr.y, acc));
   }
   block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, FIN_UPDATE, nullptr);
 }
@@ -107,11 +111,12 @@ __global__ void __launch_bounds__(VEC_NT)
 __global__ void __launch_bounds__(VEC_NT)
     dot_kernel(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
                double* partials, unsigned* ticket, DevScalars* sc, int finish, double* out_value) {
+  pdl_wait();
   double acc = 0.0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const double2 x = a[k], y = b[k];
-    acc += x.x * y.x + x.y * y.y;
+    acc = fma(x.x, y.x, fma(x.y, y.y, acc));
   }
   block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, finish, out_value);
 }
@@ -190,6 +195,7 @@ template <typename T>
 __global__ void __launch_bounds__(GEMV_NT)
     coarsest_gemv_kernel(int n, const int* __restrict__ free_idx, const double* __restrict__ Kinv,
                          const T* __restrict__ b, T* __restrict__ z, const DevScalars* sc) {
+  pdl_wait();
   if (stop_now(sc)) return;
   extern __shared__ double bs[];
   for (int k = threadIdx.x; k < n; k += GEMV_NT) bs[k] = (double)b[free_idx[k]];
@@ -229,6 +235,7 @@ __global__ void init_scalars_kernel(DevScalars* sc, double tol2, int max_it, int
 // Body condition of the solver's device-side loop: run again while the PCG
 // has not stopped.
 __global__ void set_continue_kernel(cudaGraphConditionalHandle h, const DevScalars* sc) {
+  pdl_wait();
   cudaGraphSetConditional(h, sc->done == RUNNING ? 1u : 0u);
 }
 
@@ -251,8 +258,7 @@ cudaError_t launch_init_scalars(DevScalars* sc, double tol2, int max_it, int fle
 }
 
 cudaError_t launch_set_continue(cudaGraphConditionalHandle h, const DevScalars* sc, cudaStream_t s) {
-  set_continue_kernel<<<1, 1, 0, s>>>(h, sc);
-  return cudaGetLastError();
+  return launch_pdl(set_continue_kernel, 1, 1, 0, s, h, sc);
 }
 
 cudaError_t launch_record_stats(const DevScalars* sc, RhsStats* dst, cudaStream_t s) {
@@ -262,41 +268,36 @@ cudaError_t launch_record_stats(const DevScalars* sc, RhsStats* dst, cudaStream_
 
 cudaError_t launch_jacobi0_fine64(const Grid& g, const double* invd1, const double2* r, double2* z,
                                   DevScalars* sc, int nblocks, cudaStream_t s) {
-  jacobi0_fine64_kernel<<<nblocks, VEC_NT, 0, s>>>(g, invd1, r, z, sc);
-  return cudaGetLastError();
+  return launch_pdl(jacobi0_fine64_kernel, nblocks, VEC_NT, 0, s, g, invd1, r, z, sc);
 }
 
 cudaError_t launch_jacobi0_finebf(const Grid& g, const __nv_bfloat16* E, float wdiag,
-                                  const double2* r, float2* r32, float2* z, DevScalars* sc,
-                                  int nblocks, cudaStream_t s) {
-  jacobi0_finebf_kernel<<<nblocks, VEC_NT, 0, s>>>(g, E, wdiag, r, r32, z, sc);
-  return cudaGetLastError();
+                                  const float2* r32, float2* z, DevScalars* sc, int nblocks,
+                                  cudaStream_t s) {
+  return launch_pdl(jacobi0_finebf_kernel, nblocks, VEC_NT, 0, s, g, E, wdiag, r32, z, sc);
 }
 
 template <typename T>
 cudaError_t launch_jacobi0_coarse(const Grid& g, const typename V2<T>::t* invd2,
                                   const typename V2<T>::t* b, typename V2<T>::t* z,
                                   DevScalars* sc, int nblocks, cudaStream_t s) {
-  jacobi0_coarse_kernel<T><<<nblocks, VEC_NT, 0, s>>>(g, invd2, b, z, sc);
-  return cudaGetLastError();
+  return launch_pdl(jacobi0_coarse_kernel<T>, nblocks, VEC_NT, 0, s, g, invd2, b, z, sc);
 }
 template cudaError_t launch_jacobi0_coarse<double>(const Grid&, const double2*, const double2*,
                                                    double2*, DevScalars*, int, cudaStream_t);
 template cudaError_t launch_jacobi0_coarse<float>(const Grid&, const float2*, const float2*,
                                                   float2*, DevScalars*, int, cudaStream_t);
 
-cudaError_t launch_update(const Grid& g, double2* x, double2* r, const double2* p, const double2* q,
-                          double* partials, unsigned* ticket, DevScalars* sc, int nblocks,
-                          cudaStream_t s) {
-  update_kernel<<<nblocks, VEC_NT, 0, s>>>(g.size(), x, r, p, q, partials, ticket, sc);
-  return cudaGetLastError();
+cudaError_t launch_update(const Grid& g, double2* x, double2* r, float2* r32, const double2* p,
+                          const double2* q, double* partials, unsigned* ticket, DevScalars* sc,
+                          int nblocks, cudaStream_t s) {
+  return launch_pdl(update_kernel, nblocks, VEC_NT, 0, s, g.size(), x, r, r32, p, q, partials, ticket, sc);
 }
 
 cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* partials,
                        unsigned* ticket, DevScalars* sc, int finish, double* out_value,
                        int nblocks, cudaStream_t s) {
-  dot_kernel<<<nblocks, VEC_NT, 0, s>>>(n, a, b, partials, ticket, sc, finish, out_value);
-  return cudaGetLastError();
+  return launch_pdl(dot_kernel, nblocks, VEC_NT, 0, s, n, a, b, partials, ticket, sc, finish, out_value);
 }
 
 cudaError_t launch_pack(const Grid& g, const double* src, double2* dst, cudaStream_t s, int num_sms,
@@ -330,9 +331,9 @@ cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, cons
   (void)g;
   if (n > GEMV_MAXN) return cudaErrorInvalidValue;
   const int blocks = (n + GEMV_NT / 32 - 1) / (GEMV_NT / 32);
-  coarsest_gemv_kernel<T><<<blocks, GEMV_NT, n * sizeof(double), s>>>(
-      n, free_idx, Kinv, reinterpret_cast<const T*>(b), reinterpret_cast<T*>(z), sc);
-  return cudaGetLastError();
+  return launch_pdl(coarsest_gemv_kernel<T>, blocks, GEMV_NT, n * sizeof(double), s, n, free_idx, Kinv,
+                    reinterpret_cast<const T*>(b), reinterpret_cast<T*>(z),
+                    static_cast<const DevScalars*>(sc));
 }
 template cudaError_t launch_coarsest_gemv<double>(const Grid&, int, const int*, const double*,
                                                   const double2*, double2*, DevScalars*, cudaStream_t);
