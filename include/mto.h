@@ -157,7 +157,9 @@ mto_status mto_solve_batched(int n, mto_ctx* const* ctxs, const mto_batch_item* 
  * keeps the fastest; results are cached for the process by (mesh size,
  * precision, operator kind, SM count).  Needs a design (mto_set_design) and
  * synchronises; later solves and batches use the chosen shapes.
- * mto_get_launch_shape returns the chosen (or default) warps per launch. */
+ * mto_get_launch_shape returns the chosen warps per launch, or 0 for the
+ * default: one full wave of the sweep kernel (its resident blocks per SM,
+ * set by its register use, times the SM count). */
 mto_status mto_autotune(mto_ctx* ctx);
 mto_status mto_get_launch_shape(mto_ctx* ctx, int level, int* target_warps);
 

@@ -60,13 +60,10 @@ mto_status leave(mto_ctx* c) {
 namespace mto {
 
 int target_warps(const mto_ctx* c, int level) {
-  const int t = (level >= 0 && level < MAX_LEVELS) ? c->tw[level] : 0;
-  return t > 0 ? t : c->num_sms * DEFAULT_TARGET_WARPS_PER_SM;
+  return (level >= 0 && level < MAX_LEVELS) ? c->tw[level] : 0;
 }
 
-int target_warps64(const mto_ctx* c) {
-  return c->tw64 > 0 ? c->tw64 : target_warps(c, c->L);
-}
+int target_warps64(const mto_ctx* c) { return c->tw64; }
 
 void invalidate_graphs(mto_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -96,6 +93,12 @@ template <typename T> FineConst<T> fine_const(const mto_ctx* c);
 template <> FineConst<double> fine_const<double>(const mto_ctx* c) { return c->kf64; }
 template <> FineConst<float> fine_const<float>(const mto_ctx* c) { return c->kf32; }
 
+// SRC_CMOM parameters: nu and g = (1 - nu) / 2.
+template <typename T> void set_cmom(const mto_ctx* c, SweepParams<T>& p) {
+  p.cnu = T(c->nu);
+  p.cg = T(0.5 * (1.0 - c->nu));
+}
+
 // SRC_CFINE parameters: the finest bf16 moduli and their grid.
 template <typename T> void set_cfine(const mto_ctx* c, SweepParams<T>& p) {
   p.E = c->Ebf;
@@ -118,7 +121,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   // from the bf16 fine moduli (SRC_CFINE); other coarse levels read stored
   // coefficients.
   const bool cfine = sizeof(T) == 4 && l == c->L - 1;
-  const int src = cfine ? SRC_CFINE : SRC_COARSE;
+  const int src = cfine ? SRC_CFINE : (sizeof(T) == 4 ? SRC_CMOM : SRC_COARSE);
   auto sweep = [&](int mode, const T2* v, T2* out, const T2* zc) -> cudaError_t {
     SweepParams<T> p = base_params<T>(c, L.g);
     p.gc = C.g;
@@ -131,8 +134,9 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     p.bc = (T2*)C.b;
     p.coef = (const T*)L.coef;
     p.invd2 = (const T2*)L.invd2;
+    set_cmom(c, p);
     if (cfine) set_cfine(c, p);
-    return launch_sweep<T>(src, mode, false, false, p, tw, c->cs);
+    return launch_sweep<T>(src, mode, false, false, p, tw, c->num_sms, c->cs);
   };
   // Pre-smoothing from U = 0: the first sweep (U = w D^-1 F) is formed on the
   // fly inside the second when there are two or more.
@@ -209,7 +213,7 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
       p.qdot = c->o.flexible ? c->q : nullptr;
       p.finish = FIN_RHO;
     }
-    return launch_sweep<T>(src, mode, dot, false, p, tw, c->cs);
+    return launch_sweep<T>(src, mode, dot, false, p, tw, c->num_sms, c->cs);
   };
   // Timing events bracket the first finest-level smoothing kernel.
   const bool tm = c->timing && sc != nullptr && c->cur_par >= 0;
@@ -270,7 +274,7 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.finish = finish;
   if (c->mixed && out == c->r) p.out32 = c->r32;
   KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
-                          target_warps64(c), c->cs));
+                          target_warps64(c), c->num_sms, c->cs));
   return MTO_OK;
 }
 
@@ -299,7 +303,7 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.E = c->Ek4;
     p.finish = FIN_PQ;
     KL(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
-                            target_warps64(c), c->cs));
+                            target_warps64(c), c->num_sms, c->cs));
   }
   if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->cs, cudaEventRecordExternal));
   KL(launch_update(g, c->x, c->r, c->mixed ? c->r32 : nullptr, c->p[par ^ 1], c->q, c->partials,
@@ -522,15 +526,17 @@ mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, cons
                                     c->num_sms));
     }
     if (c->mixed) {
-      KL(launch_coefs<float>(B.g, B.mom, c->nu, (float*)B.coef, c->cs, c->num_sms));
+      // Level L-1 rebuilds its elements from the bf16 fine moduli; deeper
+      // levels read scaled moments; level 0 is solved directly.
+      if (l > 0 && l < c->L - 1) KL(launch_kmom(B.g, B.mom, c->nu, (float*)B.coef, c->cs, c->num_sms));
       if (l > 0)
-        KL(launch_coarse_invd<float>(B.g, (const float*)B.coef, c->o.omega, (float2*)B.invd2, c->cs,
+        KL(launch_coarse_invd<float>(B.g, B.mom, c->nu, c->o.omega, (float2*)B.invd2, c->cs,
                                      c->num_sms));
     } else {
       KL(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->cs, c->num_sms));
       if (l > 0)
-        KL(launch_coarse_invd<double>(B.g, (const double*)B.coef, c->o.omega, (double2*)B.invd2,
-                                      c->cs, c->num_sms));
+        KL(launch_coarse_invd<double>(B.g, B.mom, c->nu, c->o.omega, (double2*)B.invd2, c->cs,
+                                      c->num_sms));
     }
   }
   LevelBuf& B0 = c->lv[0];
@@ -956,9 +962,9 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     p.out = c->q;
     p.E = c->Ek4;
     KL(launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
-                            tw, c->cs));
+                            tw, c->num_sms, c->cs));
     KL(launch_unpack(B.g, c->q, y_dev, c->cs, c->num_sms));
-  } else if (c->mixed) {
+  } else if (c->mixed && level > 0) {
     KL(launch_pack_f32(B.g, v_dev, (float2*)B.z[0], c->cs, c->num_sms));
     SweepParams<float> p = base_params<float>(c, B.g);
     p.v = (const float2*)B.z[0];
@@ -966,20 +972,26 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
     p.E = c->Ebf;
     p.kf = c->kf32;
     p.coef = (const float*)B.coef;
+    set_cmom(c, p);
     const bool cfine = level == c->L - 1;
     if (cfine) set_cfine(c, p);
-    KL(launch_sweep<float>(fine ? SRC_FINEBF : (cfine ? SRC_CFINE : SRC_COARSE), MODE_APPLY, false,
-                           false, p, tw, c->cs));
+    KL(launch_sweep<float>(fine ? SRC_FINEBF : (cfine ? SRC_CFINE : SRC_CMOM), MODE_APPLY, false,
+                           false, p, tw, c->num_sms, c->cs));
     KL(launch_unpack_f32(B.g, (const float2*)B.z[1], y_dev, c->cs, c->num_sms));
   } else {
-    KL(launch_pack(B.g, v_dev, (double2*)B.z[0], c->cs, c->num_sms));
+    // float64 coarse levels.  The mixed cycle's coarsest level is float64
+    // too; its level vectors are float2, so the finest level's float64
+    // scratch vectors (larger than any coarse grid) hold the operands.
+    double2* vin = c->mixed ? c->tmp : (double2*)B.z[0];
+    double2* vout = c->mixed ? c->q : (double2*)B.z[1];
+    KL(launch_pack(B.g, v_dev, vin, c->cs, c->num_sms));
     SweepParams<double> p = base_params<double>(c, B.g);
-    p.v = (const double2*)B.z[0];
-    p.out = (double2*)B.z[1];
-    p.coef = (const double*)B.coef;
+    p.v = vin;
+    p.out = vout;
+    p.coef = c->mixed ? B.coef64 : (const double*)B.coef;
     KL(launch_sweep<double>(SRC_COARSE, MODE_APPLY, false, false, p,
-                            tw, c->cs));
-    KL(launch_unpack(B.g, (const double2*)B.z[1], y_dev, c->cs, c->num_sms));
+                            tw, c->num_sms, c->cs));
+    KL(launch_unpack(B.g, vout, y_dev, c->cs, c->num_sms));
   }
   return leave(c);
 }

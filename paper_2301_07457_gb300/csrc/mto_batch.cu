@@ -260,7 +260,8 @@ template <typename F> static mto_status time_launches(mto_ctx* c, F launch, int 
   return MTO_OK;
 }
 
-static const int kTuneCand[] = {4, 8, 16, 32, 64, 128};
+// Target warps per SM; 0 = one full wave of the kernel (the default).
+static const int kTuneCand[] = {0, 4, 8, 12, 16, 24, 32, 48, 64};
 
 // The fastest candidate for one kind of sweep; `make` launches it with a
 // given target-warp count.
@@ -286,10 +287,8 @@ static mto_status tune_one(mto_ctx* c, const std::tuple<int, int, int, int, int>
       ST(time_launches(c, [&]() { return make(kTuneCand[k] * c->num_sms); }, 8, &ms));
       if (ms < best_of[k]) best_of[k] = ms;
     }
-  int best = c->num_sms * DEFAULT_TARGET_WARPS_PER_SM;
-  double best_ms = 1e30;
-  for (int k = 0; k < NC; ++k)
-    if (kTuneCand[k] == DEFAULT_TARGET_WARPS_PER_SM) best_ms = best_of[k];
+  int best = 0;
+  double best_ms = best_of[0];
   for (int k = 0; k < NC; ++k)
     if (best_of[k] < 0.95 * best_ms) {
       best_ms = best_of[k];
@@ -314,7 +313,7 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
     const bool f32 = c->mixed;
     const bool fine = l == c->L;
     const int src = fine ? (f32 ? SRC_FINEBF : SRC_FINE64)
-                         : (f32 && l == c->L - 1 ? SRC_CFINE : SRC_COARSE);
+                         : (f32 ? (l == c->L - 1 ? SRC_CFINE : SRC_CMOM) : SRC_COARSE);
     auto make = [&](int tw) -> cudaError_t {
       if (f32) {
         SweepParams<float> p;
@@ -329,11 +328,13 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
         p.wdiag = (float)c->w_over_kdiag;
         p.coef = (const float*)B.coef;
         p.invd2 = (const float2*)B.invd2;
+        p.cnu = (float)c->nu;
+        p.cg = (float)(0.5 * (1.0 - c->nu));
         if (src == SRC_CFINE) {
           p.gfine = c->lv[c->L].g;
           p.redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
         }
-        return launch_sweep<float>(src, MODE_SMOOTH, false, false, p, tw, c->stream);
+        return launch_sweep<float>(src, MODE_SMOOTH, false, false, p, tw, c->num_sms, c->stream);
       }
       SweepParams<double> p;
       std::memset(&p, 0, sizeof(p));
@@ -346,7 +347,7 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
       p.invd1 = c->invd1;
       p.coef = (const double*)B.coef;
       p.invd2 = (const double2*)B.invd2;
-      return launch_sweep<double>(src, MODE_SMOOTH, false, false, p, tw, c->stream);
+      return launch_sweep<double>(src, MODE_SMOOTH, false, false, p, tw, c->num_sms, c->stream);
     };
     ST(tune_one(c, std::make_tuple(B.g.nx, B.g.ny, (int)f32, src, c->num_sms), make, &c->tw[l]));
   }
@@ -363,7 +364,7 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
       p.out = c->tmp;
       p.E = c->Ek4;
       return launch_sweep<double>(SRC_FINE64, MODE_APPLY, false, false, p,
-                                  tw, c->stream);
+                                  tw, c->num_sms, c->stream);
     };
     ST(tune_one(c, std::make_tuple(g.nx, g.ny, 2, (int)SRC_FINE64, c->num_sms), make, &c->tw64));
   }

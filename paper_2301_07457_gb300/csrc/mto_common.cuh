@@ -237,6 +237,25 @@ __device__ __forceinline__ Strain<T> fine_core(const Strain<T>& w, T E, const Fi
   return t;
 }
 
+// The 13 coefficients of the table above from the six moments scaled by
+// kappa, m = kappa (M00, M10, M01, M20, M02, M11), with nu and g = (1-nu)/2.
+template <typename T>
+__host__ __device__ __forceinline__ void coefs_from_kmom(const T m[NMOM], T nu, T g, T A[NCOEF]) {
+  A[0] = m[0];
+  A[1] = m[2];
+  A[2] = m[4] + g * m[3];
+  A[3] = m[0];
+  A[4] = m[1];
+  A[5] = m[3] + g * m[4];
+  A[6] = nu * m[0];
+  A[7] = nu * m[1];
+  A[8] = nu * m[2];
+  A[9] = (nu + g) * m[5];
+  A[10] = g * m[0];
+  A[11] = g * m[1];
+  A[12] = g * m[2];
+}
+
 template <typename T>
 __device__ __forceinline__ Strain<T> coarse_core(const Strain<T>& w, const T A[NCOEF]) {
   Strain<T> t;

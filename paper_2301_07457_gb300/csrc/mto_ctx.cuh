@@ -22,8 +22,9 @@ struct LevelBuf {
 
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_RHS = 64;
-// Launch shapes: warps a sweep exposes, per SM (default and tuner range).
-constexpr int DEFAULT_TARGET_WARPS_PER_SM = 32;
+// Launch shapes: warps a sweep exposes, per SM (upper end of the tuner's
+// range).  Target 0 means one full wave of the kernel: its resident blocks
+// per SM times the SM count (the default).
 constexpr int MAX_TARGET_WARPS_PER_SM = 128;
 
 }  // namespace mto
@@ -84,8 +85,8 @@ struct mto_ctx {
   long long body_kernels = 0;         // kernels of one loop body (two iterations)
   long long launches = 0;             // kernels launched by this context (graph nodes included)
   // launch shapes: target warps of the V-cycle sweeps per level and of the
-  // float64 outer sweeps (K p, residuals) on the finest level (0 = default),
-  // set by the tuner
+  // float64 outer sweeps (K p, residuals) on the finest level (0 = one full
+  // wave of the kernel), set by the tuner
   int tw[mto::MAX_LEVELS] = {};
   int tw64 = 0;
   // optional event pairs around the hot kernels of each graph iteration:

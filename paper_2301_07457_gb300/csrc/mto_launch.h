@@ -37,24 +37,36 @@ struct SweepShape {
 SweepShape sweep_shape(const Grid& g, int mode, int target_warps, int cols);
 
 // Node columns per lane of the instantiation that launch_sweep uses for a
-// float64 (f64) or float32 sweep of source src in mode `mode`.  Two for the
-// float32 sweeps of the finest and first coarse level (issue-bound) and for
-// the float64 outer operator sweeps (K p, residuals: 3% less halo work on
-// the FP64 pipe); one for the float64 V-cycle and for levels with 13 stored
-// coefficients per element, where a pair of elements needs too many
-// registers.
+// float64 (f64) or float32 sweep of source src in mode `mode`.  Two for every
+// float32 sweep (issue- and latency-bound) and for the float64 outer
+// operator sweeps (K p, residuals: 3% less halo work on the FP64 pipe); one
+// for the float64 V-cycle, where a pair of elements (13 float64 coefficients
+// each on coarse levels) needs too many registers.
 constexpr int sweep_cols_of(bool f64, int src, int mode) {
   if (f64) {
     return (src == SRC_FINE64 && (mode == MODE_KP || mode == MODE_RESID || mode == MODE_APPLY)) ? 2 : 1;
   }
-  return src == SRC_COARSE ? 1 : 2;
+  return 2;
 }
 int sweep_cols(bool f64, int src, int mode);
 
-// Launch one sweep over p.g; the launch shape follows from target_warps.
+// Launch one sweep over p.g; the launch shape follows from target_warps
+// (0: one full wave of the kernel on num_sms SMs).
 template <typename T>
 cudaError_t launch_sweep(int src, int mode, bool dot, bool zfloat, SweepParams<T> p,
-                         int target_warps, cudaStream_t s);
+                         int target_warps, int num_sms, cudaStream_t s);
+
+// Warps of one full wave of a sweep kernel: resident blocks per SM (from its
+// registers) times the SM count.
+template <typename K> int full_wave_warps(K kernel, int num_sms) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, SWEEP_NT, 0) != cudaSuccess ||
+      blocks < 1) {
+    cudaGetLastError();
+    blocks = 1;
+  }
+  return blocks * (SWEEP_NT / 32) * num_sms;
+}
 
 // ---- pointwise kernels (mto_vec.cu) ----
 constexpr int VEC_NT = 256;
@@ -124,9 +136,13 @@ cudaError_t launch_moments_from_coarse(const Grid& gc, const Grid& gf, const dou
 template <typename T>
 cudaError_t launch_coefs(const Grid& g, const double* mom, double nu, T* coef, cudaStream_t s,
                          int num_sms);
+// w / D per DOF of a coarse level from its float64 element moments.
 template <typename T>
-cudaError_t launch_coarse_invd(const Grid& g, const T* coef, double omega,
+cudaError_t launch_coarse_invd(const Grid& g, const double* mom, double nu, double omega,
                                typename V2<T>::t* invd2, cudaStream_t s, int num_sms);
+// kappa-scaled float32 moments of a float32 coarse level (SRC_CMOM).
+cudaError_t launch_kmom(const Grid& g, const double* mom, double nu, float* out, cudaStream_t s,
+                        int num_sms);
 // Coarsest matrix from float64 coefficients of level 0, lower band storage
 // Kb[r * (bw + 1) + d] = K_0[r][r - d] (zeroed by the caller).
 cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,

@@ -150,38 +150,63 @@ __global__ void coefs_kernel(Grid g, const double* __restrict__ mom, double nu, 
 // Diagonal of an element matrix J^T A J at local node q (0 BL, 1 BR, 2 TR, 3 TL):
 // J column of u_x at q is (s1, s3, 0, 0, s2), of u_y is (0, 0, s2, s3, s1), with
 // s1 = (-1, 1, 1, -1), s2 = (-1, -1, 1, 1), s3 = (1, -1, 1, -1); s1 s3 = s2, s2 s3 = s1.
-template <typename T>
-__device__ __forceinline__ void elem_diag(const T* coef, long long s, long long k, int q, double& dx,
-                                          double& dy) {
+__device__ __forceinline__ void elem_diag(const double A[NCOEF], int q, double& dx, double& dy) {
   const double s1 = (q == 1 || q == 2) ? 1.0 : -1.0;
   const double s2 = (q >= 2) ? 1.0 : -1.0;
-  const double A0 = coef[k], A1 = coef[s + k], A2 = coef[2 * s + k], A3 = coef[3 * s + k];
-  const double A4 = coef[4 * s + k], A5 = coef[5 * s + k], A10 = coef[10 * s + k];
-  const double A11 = coef[11 * s + k], A12 = coef[12 * s + k];
-  dx += A0 + A2 + A10 + 2.0 * s2 * A1 + 2.0 * s1 * A11;
-  dy += A3 + A5 + A10 + 2.0 * s1 * A4 + 2.0 * s2 * A12;
+  dx += A[0] + A[2] + A[10] + 2.0 * s2 * A[1] + 2.0 * s1 * A[11];
+  dy += A[3] + A[5] + A[10] + 2.0 * s1 * A[4] + 2.0 * s2 * A[12];
 }
 
+// Coefficients of element k from the float64 moments (zero for ghost elements).
+__device__ __forceinline__ void coefs_at(const double* __restrict__ mom, long long s, long long k,
+                                         double kap, double nu, double gs, double A[NCOEF]) {
+  double m[NMOM];
+#pragma unroll
+  for (int c = 0; c < NMOM; ++c) m[c] = kap * mom[c * s + k];
+  coefs_from_kmom<double>(m, nu, gs, A);
+}
+
+// w / D per DOF of a coarse level, from the float64 moments of its elements.
 template <typename T>
-__global__ void coarse_invd_kernel(Grid g, const T* __restrict__ coef, double omega,
+__global__ void coarse_invd_kernel(Grid g, const double* __restrict__ mom, double nu, double omega,
                                    typename V2<T>::t* __restrict__ invd2) {
   const long long n = (long long)(g.nx + 1) * (g.ny + 1);
   const long long s = g.size();
+  const double kap = 1.0 / (4.0 * (1.0 - nu * nu)), gs = 0.5 * (1.0 - nu);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
     const long long k = g.at(i, j);
     typename V2<T>::t out = mk2<T>(T(0), T(0));
     if (!g.is_fixed(i, j)) {
-      double dx = 0.0, dy = 0.0;
-      // Ghost elements have zero coefficients, so all four may be visited.
-      elem_diag(coef, s, k - g.pitch - 1, 2, dx, dy);  // element (i-1, j-1): node is TR
-      elem_diag(coef, s, k - g.pitch, 3, dx, dy);      // element (i, j-1): TL
-      elem_diag(coef, s, k - 1, 1, dx, dy);            // element (i-1, j): BR
-      elem_diag(coef, s, k, 0, dx, dy);                // element (i, j): BL
+      double dx = 0.0, dy = 0.0, A[NCOEF];
+      // Ghost elements have zero moments, so all four may be visited.
+      coefs_at(mom, s, k - g.pitch - 1, kap, nu, gs, A);
+      elem_diag(A, 2, dx, dy);  // element (i-1, j-1): node is TR
+      coefs_at(mom, s, k - g.pitch, kap, nu, gs, A);
+      elem_diag(A, 3, dx, dy);  // element (i, j-1): TL
+      coefs_at(mom, s, k - 1, kap, nu, gs, A);
+      elem_diag(A, 1, dx, dy);  // element (i-1, j): BR
+      coefs_at(mom, s, k, kap, nu, gs, A);
+      elem_diag(A, 0, dx, dy);  // element (i, j): BL
       out = mk2<T>(T(omega / dx), T(omega / dy));
     }
     invd2[k] = out;
+  }
+}
+
+// Six kappa-scaled float32 moments per element of a float32 coarse level
+// (SRC_CMOM sweeps).
+__global__ void kmom_kernel(Grid g, const double* __restrict__ mom, double nu, float* __restrict__ out) {
+  const long long n = (long long)g.nx * g.ny;
+  const long long s = g.size();
+  const double kap = 1.0 / (4.0 * (1.0 - nu * nu));
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % g.nx), J = (int)(t / g.nx);
+    const long long k = g.at(I, J);
+#pragma unroll
+    for (int c = 0; c < NMOM; ++c) out[c * s + k] = (float)(kap * mom[c * s + k]);
   }
 }
 
@@ -452,16 +477,22 @@ template cudaError_t launch_coefs<double>(const Grid&, const double*, double, do
 template cudaError_t launch_coefs<float>(const Grid&, const double*, double, float*, cudaStream_t, int);
 
 template <typename T>
-cudaError_t launch_coarse_invd(const Grid& g, const T* coef, double omega,
+cudaError_t launch_coarse_invd(const Grid& g, const double* mom, double nu, double omega,
                                typename V2<T>::t* invd2, cudaStream_t s, int num_sms) {
   coarse_invd_kernel<T><<<blocks_for((long long)(g.nx + 1) * (g.ny + 1), num_sms), 256, 0, s>>>(
-      g, coef, omega, invd2);
+      g, mom, nu, omega, invd2);
   return cudaGetLastError();
 }
-template cudaError_t launch_coarse_invd<double>(const Grid&, const double*, double, double2*,
+template cudaError_t launch_coarse_invd<double>(const Grid&, const double*, double, double, double2*,
                                                 cudaStream_t, int);
-template cudaError_t launch_coarse_invd<float>(const Grid&, const float*, double, float2*,
+template cudaError_t launch_coarse_invd<float>(const Grid&, const double*, double, double, float2*,
                                                cudaStream_t, int);
+
+cudaError_t launch_kmom(const Grid& g, const double* mom, double nu, float* out, cudaStream_t s,
+                        int num_sms) {
+  kmom_kernel<<<blocks_for((long long)g.nx * g.ny, num_sms), 256, 0, s>>>(g, mom, nu, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
                                  int bw, double* Kb, cudaStream_t s) {

@@ -49,7 +49,10 @@ constexpr int SWEEP_RSTRIDE = 28;
 // SRC_CFINE: the first coarse level of the mixed path, whose Galerkin element
 // matrices are rebuilt on the fly from the four bf16 fine moduli they cover
 // (8 bytes per coarse element instead of 13 stored coefficients).
-enum Src { SRC_FINE64 = 0, SRC_FINEBF = 1, SRC_COARSE = 2, SRC_CFINE = 3 };
+// SRC_CMOM: the deeper float32 coarse levels, which store the six scaled
+// moments of each element (24 bytes) and form the 13 coefficients in
+// registers.
+enum Src { SRC_FINE64 = 0, SRC_FINEBF = 1, SRC_COARSE = 2, SRC_CFINE = 3, SRC_CMOM = 4 };
 enum Mode {
   MODE_APPLY = 0,
   MODE_RESID,
@@ -77,8 +80,9 @@ template <typename T> struct SweepParams {
   float2* out32;     // RESID: optional float32 copy of out (the mixed V-cycle's input)
   T2* bc;            // RESTRICT: coarse right-hand side
   const void* E;     // finest level: 4 scaled float64 moduli per element (FINE64) or bf16 E
-  const T* coef;     // coarse element matrices, NCOEF arrays of g.size()
+  const T* coef;     // coarse element matrices, NCOEF arrays of g.size() (SRC_CMOM: NMOM moments)
   long long cstride;
+  T cnu, cg;         // SRC_CMOM: nu and g = (1 - nu) / 2
   FineConst<T> kf;      // bf16 finest level / SRC_CFINE: scale factors of the element core
   Grid gfine;           // SRC_CFINE: the finer grid whose bf16 moduli E points to
   int redisc;           // SRC_CFINE: rediscretised (mean modulus) instead of Galerkin
@@ -138,6 +142,9 @@ template <typename T> struct ERaw<T, SRC_COARSE> {
 };
 template <typename T> struct ERaw<T, SRC_CFINE> {
   __nv_bfloat162 lo, hi;  // fine moduli of rows 2J and 2J+1, columns 2I and 2I+1
+};
+template <typename T> struct ERaw<T, SRC_CMOM> {
+  T m[NMOM];
 };
 
 // Loads that belong to the node row being completed.
@@ -224,6 +231,9 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
       r.k23 = __ldg(p + 1);
     } else if constexpr (SRC == SRC_FINEBF) {
       r.E = static_cast<const __nv_bfloat16*>(a.E)[e];
+    } else if constexpr (SRC == SRC_CMOM) {
+#pragma unroll
+      for (int c = 0; c < NMOM; ++c) r.m[c] = a.coef[c * a.cstride + e];
     } else {
 #pragma unroll
       for (int c = 0; c < NCOEF; ++c) r.A[c] = a.coef[c * a.cstride + e];
@@ -234,7 +244,7 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
     if constexpr (NEEDS_B) r.b = a.b[k];
     if constexpr (SMOOTHING) {
       if constexpr (SRC == SRC_FINE64) r.d1 = a.invd1[k];
-      else if constexpr (SRC == SRC_COARSE || SRC == SRC_CFINE) r.d2 = a.invd2[k];
+      else if constexpr (SRC == SRC_COARSE || SRC == SRC_CFINE || SRC == SRC_CMOM) r.d2 = a.invd2[k];
       if constexpr (DOT) {
         r.rd = a.rdot[k];
         if (a.qdot != nullptr) r.qd = a.qdot[k];
@@ -282,6 +292,10 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep {
       A[10] = k.kG * M00;
       A[11] = k.kG * M10;
       A[12] = k.kG * M01;
+      t = coarse_core<T>(w, A);
+    } else if constexpr (SRC == SRC_CMOM) {
+      T A[NCOEF];
+      coefs_from_kmom<T>(er.m, a.cnu, a.cg, A);
       t = coarse_core<T>(w, A);
     } else {
       t = coarse_core<T>(w, er.A);

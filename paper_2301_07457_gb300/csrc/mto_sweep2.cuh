@@ -67,6 +67,9 @@ template <typename T> struct ERaw2<T, SRC_COARSE> {
 template <typename T> struct ERaw2<T, SRC_CFINE> {
   __nv_bfloat162 lo[2], hi[2];  // fine moduli of rows 2J, 2J+1; [w] = coarse element i0 + w
 };
+template <typename T> struct ERaw2<T, SRC_CMOM> {
+  typename V2<T>::t m[NMOM];
+};
 
 template <typename T>
 __device__ __forceinline__ ERaw<T, SRC_FINE64> pick(const ERaw2<T, SRC_FINE64>& r, int w) {
@@ -80,6 +83,13 @@ __device__ __forceinline__ ERaw<T, SRC_COARSE> pick(const ERaw2<T, SRC_COARSE>& 
   ERaw<T, SRC_COARSE> e;
 #pragma unroll
   for (int c = 0; c < NCOEF; ++c) e.A[c] = w ? r.A[c].y : r.A[c].x;
+  return e;
+}
+template <typename T>
+__device__ __forceinline__ ERaw<T, SRC_CMOM> pick(const ERaw2<T, SRC_CMOM>& r, int w) {
+  ERaw<T, SRC_CMOM> e;
+#pragma unroll
+  for (int c = 0; c < NMOM; ++c) e.m[c] = w ? r.m[c].y : r.m[c].x;
   return e;
 }
 template <typename T>
@@ -225,6 +235,10 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep2 {
       // SMOOTH0 forms D at both columns of the top row, so every lane needs
       // the modulus of element i0 - 1 itself (lane 0 has no left lane).
       if constexpr (MODE == MODE_SMOOTH0) r.El = *reinterpret_cast<const __nv_bfloat162*>(Eb + e - 2);
+    } else if constexpr (SRC == SRC_CMOM) {
+      using T2c = typename V2<T>::t;
+#pragma unroll
+      for (int c = 0; c < NMOM; ++c) r.m[c] = *reinterpret_cast<const T2c*>(a.coef + c * a.cstride + e);
     } else {
       using T2c = typename V2<T>::t;
 #pragma unroll
@@ -236,7 +250,7 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep2 {
     if constexpr (NEEDS_B) ld_pair(a.b, k, r.b0, r.b1);
     if constexpr (SMOOTHING && MODE != MODE_SMOOTH0) {
       if constexpr (SRC == SRC_FINE64) r.d1 = reinterpret_cast<const double2*>(a.invd1)[k >> 1];
-      else if constexpr (SRC == SRC_COARSE || SRC == SRC_CFINE) ld_pair(a.invd2, k, r.d20, r.d21);
+      else if constexpr (SRC == SRC_COARSE || SRC == SRC_CFINE || SRC == SRC_CMOM) ld_pair(a.invd2, k, r.d20, r.d21);
     }
   }
 

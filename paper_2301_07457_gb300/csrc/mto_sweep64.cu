@@ -36,47 +36,50 @@ SweepShape sweep_shape(const Grid& g, int mode, int target_warps, int cols) {
 int sweep_cols(bool f64, int src, int mode) { return sweep_cols_of(f64, src, mode); }
 
 template <int SRC, int MODE, bool DOT, typename ZT>
-static cudaError_t go(SweepParams<double> p, int tw, cudaStream_t s) {
+static cudaError_t go(SweepParams<double> p, int tw, int num_sms, cudaStream_t s) {
   constexpr int COLS = sweep_cols_of(true, SRC, MODE);
+  void (*kernel)(SweepParams<double>);
+  if constexpr (COLS == 2) kernel = sweep2_kernel<double, SRC, MODE, DOT, ZT, 1>;
+  else kernel = sweep_kernel<double, SRC, MODE, DOT, ZT, 1>;
+  if (tw <= 0) {
+    static const int wave = full_wave_warps(kernel, num_sms);  // same for every device of a run
+    tw = wave;
+  }
   const SweepShape sh = sweep_shape(p.g, MODE, tw, COLS);
   p.nstrips = sh.nstrips;
   p.nchunks = sh.nchunks;
   p.H = sh.H;
-  if constexpr (COLS == 2) {
-    return launch_pdl(sweep2_kernel<double, SRC, MODE, DOT, ZT, 1>, sh.nblocks, SWEEP_NT, 0, s, p);
-  } else {
-    return launch_pdl(sweep_kernel<double, SRC, MODE, DOT, ZT, 1>, sh.nblocks, SWEEP_NT, 0, s, p);
-  }
+  return launch_pdl(kernel, sh.nblocks, SWEEP_NT, 0, s, p);
 }
 
 template <>
 cudaError_t launch_sweep<double>(int src, int mode, bool dot, bool zfloat, SweepParams<double> p,
-                                 int tw, cudaStream_t s) {
+                                 int tw, int num_sms, cudaStream_t s) {
   if (src == SRC_FINE64) {
     switch (mode) {
-      case MODE_APPLY: return go<SRC_FINE64, MODE_APPLY, false, double2>(p, tw, s);
-      case MODE_RESID: return go<SRC_FINE64, MODE_RESID, false, double2>(p, tw, s);
+      case MODE_APPLY: return go<SRC_FINE64, MODE_APPLY, false, double2>(p, tw, num_sms, s);
+      case MODE_RESID: return go<SRC_FINE64, MODE_RESID, false, double2>(p, tw, num_sms, s);
       case MODE_KP:
-        return zfloat ? go<SRC_FINE64, MODE_KP, false, float2>(p, tw, s)
-                      : go<SRC_FINE64, MODE_KP, false, double2>(p, tw, s);
+        return zfloat ? go<SRC_FINE64, MODE_KP, false, float2>(p, tw, num_sms, s)
+                      : go<SRC_FINE64, MODE_KP, false, double2>(p, tw, num_sms, s);
       case MODE_SMOOTH:
-        return dot ? go<SRC_FINE64, MODE_SMOOTH, true, double2>(p, tw, s)
-                   : go<SRC_FINE64, MODE_SMOOTH, false, double2>(p, tw, s);
-      case MODE_SMOOTH0: return go<SRC_FINE64, MODE_SMOOTH0, false, double2>(p, tw, s);
+        return dot ? go<SRC_FINE64, MODE_SMOOTH, true, double2>(p, tw, num_sms, s)
+                   : go<SRC_FINE64, MODE_SMOOTH, false, double2>(p, tw, num_sms, s);
+      case MODE_SMOOTH0: return go<SRC_FINE64, MODE_SMOOTH0, false, double2>(p, tw, num_sms, s);
       case MODE_PSMOOTH:
-        return dot ? go<SRC_FINE64, MODE_PSMOOTH, true, double2>(p, tw, s)
-                   : go<SRC_FINE64, MODE_PSMOOTH, false, double2>(p, tw, s);
-      case MODE_RESTRICT: return go<SRC_FINE64, MODE_RESTRICT, false, double2>(p, tw, s);
+        return dot ? go<SRC_FINE64, MODE_PSMOOTH, true, double2>(p, tw, num_sms, s)
+                   : go<SRC_FINE64, MODE_PSMOOTH, false, double2>(p, tw, num_sms, s);
+      case MODE_RESTRICT: return go<SRC_FINE64, MODE_RESTRICT, false, double2>(p, tw, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }
   if (src == SRC_COARSE) {
     switch (mode) {
-      case MODE_APPLY: return go<SRC_COARSE, MODE_APPLY, false, double2>(p, tw, s);
-      case MODE_SMOOTH: return go<SRC_COARSE, MODE_SMOOTH, false, double2>(p, tw, s);
-      case MODE_SMOOTH0: return go<SRC_COARSE, MODE_SMOOTH0, false, double2>(p, tw, s);
-      case MODE_PSMOOTH: return go<SRC_COARSE, MODE_PSMOOTH, false, double2>(p, tw, s);
-      case MODE_RESTRICT: return go<SRC_COARSE, MODE_RESTRICT, false, double2>(p, tw, s);
+      case MODE_APPLY: return go<SRC_COARSE, MODE_APPLY, false, double2>(p, tw, num_sms, s);
+      case MODE_SMOOTH: return go<SRC_COARSE, MODE_SMOOTH, false, double2>(p, tw, num_sms, s);
+      case MODE_SMOOTH0: return go<SRC_COARSE, MODE_SMOOTH0, false, double2>(p, tw, num_sms, s);
+      case MODE_PSMOOTH: return go<SRC_COARSE, MODE_PSMOOTH, false, double2>(p, tw, num_sms, s);
+      case MODE_RESTRICT: return go<SRC_COARSE, MODE_RESTRICT, false, double2>(p, tw, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -119,7 +119,8 @@ def test_autotune_keeps_results(mto, prec):
     u0, s0 = m.solve(f)
     shapes = m.autotune()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert all(s % sms == 0 and 4 <= s // sms <= 128 for s in shapes)
+    # 0 = one full wave of the kernel (default), else warps per launch.
+    assert all(s == 0 or (s % sms == 0 and 4 <= s // sms <= 128) for s in shapes)
     u1, s1 = m.solve(f)
     # Launch shapes change summation order only: same convergence, same answer.
     assert abs(s1["iters"] - s0["iters"]) <= 1
