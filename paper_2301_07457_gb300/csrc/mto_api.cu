@@ -259,8 +259,11 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
 }
 
 // out = b - K v on the finest level in float64 (RESID), with a finishing action.
+// With xlag, the sweep works on v + alpha xdir while the device scalars say
+// that the x step is pending (residual replacement inside the loop).
 mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* out, int finish,
-                      int gate, int replace_gate, int zero_gate = 0) {
+                      int gate, int replace_gate, int zero_gate = 0, int xlag = 0,
+                      const double2* xdir = nullptr) {
   const Grid& g = c->lv[c->L].g;
   SweepParams<double> p = base_params<double>(c, g);
   p.gate = gate;
@@ -272,6 +275,8 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.out = out;
   p.E = c->Ek4;
   p.finish = finish;
+  p.xlag = xlag;
+  p.xdir = xdir;
   if (c->mixed && out == c->r) p.out32 = c->r32;
   KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
                           target_warps64(c), c->num_sms, c->cs));
@@ -299,6 +304,8 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.v = c->p[par];
     p.zkp = z;
     p.p_out = c->p[par ^ 1];
+    p.xvec = c->x;
+    p.tag = par ^ 1;
     p.out = c->q;
     p.E = c->Ek4;
     p.finish = FIN_PQ;
@@ -306,10 +313,10 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
                             target_warps64(c), c->num_sms, c->cs));
   }
   if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->cs, cudaEventRecordExternal));
-  KL(launch_update(g, c->x, c->r, c->mixed ? c->r32 : nullptr, c->p[par ^ 1], c->q, c->partials,
-                   c->ticket, c->sc,
+  KL(launch_update(g, c->r, c->mixed ? c->r32 : nullptr, c->q, c->partials, c->ticket, c->sc,
                    vec_blocks(g.size(), c->num_sms), c->cs));
-  if (c->mixed && c->o.rr_every > 0) ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1));
+  if (c->mixed && c->o.rr_every > 0)
+    ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1, 0, 1, c->p[par ^ 1]));
   return MTO_OK;
 }
 
@@ -406,6 +413,7 @@ mto_status solve_polled(mto_ctx* c) {
       launched += 2;
     }
   }
+  KL(launch_x_step(g, c->x, c->p[0], c->p[1], c->sc, vec_blocks(g.size(), c->num_sms), c->stream));
   ST(fine_resid(c, c->x, c->f, c->tmp, FIN_TRUE, 0, 0));
   return MTO_OK;
 }
@@ -482,6 +490,7 @@ mto_status enqueue_solve_core(mto_ctx* c) {
     g_last_cuda = e;
     return MTO_ERR_CUDA;
   }
+  KL(launch_x_step(g, c->x, c->p[0], c->p[1], c->sc, vec_blocks(g.size(), c->num_sms), c->cs));
   ST(fine_resid(c, c->x, c->f, c->tmp, FIN_TRUE, 0, 0));
   return MTO_OK;
 }

@@ -285,6 +285,11 @@ struct DevScalars {
   double dot;       // scratch result of a plain dot kernel
   int iter, max_it, done, flexible, rr_every;
   int x_nonzero;    // set by the packing of the warm start when any entry is non-zero
+  // The CG update applies r -= alpha q at once but x += alpha p one step
+  // late, inside the next K p sweep (which loads p there anyway and is not
+  // bound by memory): x_lag = 1 while x is one step behind, p_par says which
+  // search-direction buffer holds that p.
+  int x_lag, p_par;
 };
 
 // Outcome of one solve, copied from DevScalars at the end of each right-hand side.
@@ -308,7 +313,8 @@ enum Finish {
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
 
-__device__ __forceinline__ void finish_scalars(DevScalars* sc, int kind, double s0, double s1) {
+__device__ __forceinline__ void finish_scalars(DevScalars* sc, int kind, double s0, double s1,
+                                               int tag) {
   switch (kind) {
     case FIN_DOT: sc->dot = s0; break;
     case FIN_FF: sc->ff = s0; break;
@@ -331,11 +337,15 @@ __device__ __forceinline__ void finish_scalars(DevScalars* sc, int kind, double 
       break;
     }
     case FIN_PQ:
+      // The K p sweep has applied any pending x step; p[tag] is the new p.
+      sc->x_lag = 0;
+      sc->p_par = tag;
       sc->pq = s0;
       if (!finite_pos(s0)) { sc->done = BREAKDOWN; break; }
       sc->alpha = sc->rho / s0;
       break;
     case FIN_UPDATE: {
+      sc->x_lag = 1;
       sc->rr = s0;
       sc->iter += 1;
       sc->rho_prev = sc->rho;
@@ -363,7 +373,7 @@ __device__ __forceinline__ void finish_scalars(DevScalars* sc, int kind, double 
 template <int NT>
 __device__ __forceinline__ void block_reduce_finish(double v0, double v1, double* partials,
                                                     unsigned* ticket, DevScalars* sc, int kind,
-                                                    double* out_value) {
+                                                    double* out_value, int tag = 0) {
   __shared__ double red[2][NT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -416,7 +426,7 @@ __device__ __forceinline__ void block_reduce_finish(double v0, double v1, double
       s0 += red[0][w];
       s1 += red[1][w];
     }
-    if (sc) finish_scalars(sc, kind, s0, s1);
+    if (sc) finish_scalars(sc, kind, s0, s1, tag);
     if (out_value) out_value[0] = s0;
     *ticket = 0u;
     __threadfence();

@@ -84,10 +84,14 @@ cudaError_t launch_jacobi0_coarse(const Grid& g, const typename V2<T>::t* invd2,
                                   const typename V2<T>::t* b, typename V2<T>::t* z,
                                   DevScalars* sc, int nblocks, cudaStream_t s);
 // x += alpha p; r -= alpha q; rr = |r|^2 (FIN_UPDATE).
-// x += alpha p, r -= alpha q, rr = |r|^2 (FIN_UPDATE); r32 = float(r) when not null.
-cudaError_t launch_update(const Grid& g, double2* x, double2* r, float2* r32, const double2* p,
-                          const double2* q, double* partials, unsigned* ticket, DevScalars* sc,
-                          int nblocks, cudaStream_t s);
+// r -= alpha q, rr = |r|^2 (FIN_UPDATE: the x step becomes pending); r32 =
+// float(r) when not null.
+cudaError_t launch_update(const Grid& g, double2* r, float2* r32, const double2* q,
+                          double* partials, unsigned* ticket, DevScalars* sc, int nblocks,
+                          cudaStream_t s);
+// x += alpha p[p_par] when the x step is pending (after the PCG loop).
+cudaError_t launch_x_step(const Grid& g, double2* x, const double2* p0, const double2* p1,
+                          const DevScalars* sc, int nblocks, cudaStream_t s);
 // sum a.b over n double2 values (finish kind applied to sc, result also to out_value).
 cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* partials,
                        unsigned* ticket, DevScalars* sc, int finish, double* out_value,

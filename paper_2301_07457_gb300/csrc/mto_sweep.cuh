@@ -75,6 +75,10 @@ template <typename T> struct SweepParams {
   const T2* zc;      // PSMOOTH: coarse correction
   const void* zkp;   // KP: z (double2 or float2)
   T2* p_out;         // KP: new search direction
+  T2* xvec;          // KP: the iterate x, advanced by the pending step alpha p_old (x_lag)
+  const T2* xdir;    // RESID with xlag: the direction p of the pending step
+  int xlag;          // RESID: apply the pending step to v on the fly (v = x + alpha p) when x_lag
+  int tag;           // KP: index of p_out among the two search-direction buffers
   const T2* b;       // right-hand side (SMOOTH, SMOOTH0, PSMOOTH, RESTRICT, RESID)
   T2* out;           // output vector (APPLY, RESID, KP: q, SMOOTH*, PSMOOTH)
   float2* out32;     // RESID: optional float32 copy of out (the mixed V-cycle's input)

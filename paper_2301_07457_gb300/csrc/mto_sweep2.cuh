@@ -137,10 +137,14 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep2 {
   // bf16 finest moduli run one row ahead of the elements.
   static constexpr bool E_AHEAD = SRC == SRC_FINEBF;
 
-  // k: offset of node (i0, jj); i0 even.
+  // k: offset of node (i0, jj); i0 even.  lag (RESID): also load the
+  // direction of the pending x step.
   __device__ __forceinline__ static void load_v(const SweepParams<T>& a, long long k, int i0, int jj,
-                                                VR& r) {
-    if constexpr (MODE == MODE_KP) {
+                                                VR& r, bool lag = false) {
+    if constexpr (MODE == MODE_RESID) {
+      ld_pair(a.v, k, r.v0, r.v1);
+      if (lag) ld_pair(a.xdir, k, r.z0, r.z1);
+    } else if constexpr (MODE == MODE_KP) {
       ld_pair(static_cast<const ZT*>(a.zkp), k, r.z0, r.z1);
       ld_pair(a.v, k, r.v0, r.v1);
     } else if constexpr (MODE == MODE_PSMOOTH) {
@@ -172,8 +176,16 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep2 {
   // Marched values of the pair at row jj (SMOOTH0 on the bf16 level is formed
   // in the kernel, where the top-row D is known).
   __device__ __forceinline__ static void finish_v(const SweepParams<T>& a, const VR& r, int i0, int jj,
-                                                  T beta, T2& o0, T2& o1) {
-    if constexpr (MODE == MODE_KP) {
+                                                  T beta, T2& o0, T2& o1, bool lag = false,
+                                                  T alag = T(0)) {
+    if constexpr (MODE == MODE_RESID) {
+      o0 = r.v0;
+      o1 = r.v1;
+      if (lag) {  // x + alpha p: the iterate the pending step leads to
+        o0 = mk2<T>(fma(alag, T(r.z0.x), o0.x), fma(alag, T(r.z0.y), o0.y));
+        o1 = mk2<T>(fma(alag, T(r.z1.x), o1.x), fma(alag, T(r.z1.y), o1.y));
+      }
+    } else if constexpr (MODE == MODE_KP) {
       if constexpr (sizeof(T) == 8) {
         o0 = mk2<T>(to_f64(r.z0.x) + beta * r.v0.x, to_f64(r.z0.y) + beta * r.v0.y);
         o1 = mk2<T>(to_f64(r.z1.x) + beta * r.v1.x, to_f64(r.z1.y) + beta * r.v1.y);
@@ -295,8 +307,10 @@ __device__ __forceinline__ void fbf_winv_own(float ebl, float eb0, float eb1, fl
 __device__ __forceinline__ float bf_lo(__nv_bfloat162 v) { return __low2float(v); }
 __device__ __forceinline__ float bf_hi(__nv_bfloat162 v) { return __high2float(v); }
 
+// Two resident blocks per SM (at most 128 registers per thread): one full
+// wave is then 16 warps per SM, which the launch shapes assume.
 template <typename T, int SRC, int MODE, bool DOT, typename ZT, int PF>
-__global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a) {
+__global__ void __launch_bounds__(SWEEP_NT, 2) sweep2_kernel(const SweepParams<T> a) {
   using T2 = typename V2<T>::t;
   using S2 = Sweep2<T, SRC, MODE, DOT, ZT>;
   using VR = typename S2::VR;
@@ -319,6 +333,20 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
   if constexpr (MODE == MODE_KP) beta = T(a.sc->beta);
   bool vzero = false;
   if constexpr (MODE == MODE_RESID) vzero = a.zero_gate && a.sc->x_nonzero == 0;
+  // Pending x step (x_lag): K p advances x at its owned nodes, the residual
+  // replacement works on x + alpha p.
+  bool lag = false;
+  T alag = T(0);
+  if constexpr (MODE == MODE_KP) {
+    lag = a.sc->x_lag != 0;
+    alag = T(a.sc->alpha);
+  }
+  if constexpr (MODE == MODE_RESID) {
+    if (a.xlag && a.sc != nullptr && a.sc->x_lag != 0) {
+      lag = true;
+      alag = T(a.sc->alpha);
+    }
+  }
 
   constexpr int STRIDE = MODE == MODE_RESTRICT ? SWEEP2_RSTRIDE : SWEEP2_STRIDE;
   const Grid g = a.g;
@@ -369,7 +397,7 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
     // Step je: node row je + 1, element row je (je + 1 for the bf16 moduli),
     // node row je.
     auto load_pack = [&](Pack& pk, int je, long long ke) {
-      S2::load_v(a, ke + pitch, i0, je + 1, pk.vt);
+      S2::load_v(a, ke + pitch, i0, je + 1, pk.vt, lag);
       if constexpr (S2::E_AHEAD) S2::load_e(a, ke + pitch, i0, je + 1, pk.e);
       else S2::load_e(a, ke, i0, je, pk.e);
       S2::load_n(a, ke, pk.n);
@@ -401,7 +429,7 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
     T2 vb0, vb1;
     {
       VR r0;
-      S2::load_v(a, k0, i0, je0, r0);
+      S2::load_v(a, k0, i0, je0, r0, lag);
       if constexpr (FBF0) {
         float w0, w1;
         fbf_winv_own(epl, ep0, ep1, ecl, ec0, ec1, float(a.wdiag), w0, w1);
@@ -414,7 +442,7 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
         vb0 = mk2<T>(wc0.x * r0.v0.x, wc0.y * r0.v0.y);
         vb1 = mk2<T>(wc1.x * r0.v1.x, wc1.y * r0.v1.y);
       } else {
-        S2::finish_v(a, r0, i0, je0, beta, vb0, vb1);
+        S2::finish_v(a, r0, i0, je0, beta, vb0, vb1, lag, alag);
       }
       if constexpr (MODE == MODE_SMOOTH0) {
         bc0 = r0.v0;
@@ -456,6 +484,18 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
         if (je > je1) break;
         const Pack cur = ring[u];
         if (je + PF <= je1) load_pack(ring[u], je + PF, k + PF * pitch);
+        if constexpr (MODE == MODE_KP) {
+          // Pending x step at the top row (owned rows only): x += alpha p_old.
+          // Done at once, so that x occupies registers only briefly; other
+          // warps cover the load with FP64 work.
+          if (lag && je + 1 <= je1) {  // uniform over the warp
+            T2 x0, x1;
+            ld_pair(a.xvec, k + pitch, x0, x1);
+            x0 = mk2<T>(fma(alag, cur.vt.v0.x, x0.x), fma(alag, cur.vt.v0.y, x0.y));
+            x1 = mk2<T>(fma(alag, cur.vt.v1.x, x1.x), fma(alag, cur.vt.v1.y, x1.y));
+            st_pair(a.xvec, k + pitch, x0, x1, own0, own1);
+          }
+        }
         if constexpr (DOT) {
           if (je > je0) {
             dcur = dnext;
@@ -485,8 +525,9 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
           vt0 = mk2<T>(wt0.x * cur.vt.v0.x, wt0.y * cur.vt.v0.y);
           vt1 = mk2<T>(wt1.x * cur.vt.v1.x, wt1.y * cur.vt.v1.y);
         } else {
-          S2::finish_v(a, cur.vt, i0, je + 1, beta, vt0, vt1);
+          S2::finish_v(a, cur.vt, i0, je + 1, beta, vt0, vt1, lag, alag);
         }
+
         const T2 vt2 = shfl_down2(vt0);  // lane 31: its own value, used only for halo output
         const T2 bt0 = sub2(vt1, vt0), bt1 = sub2(vt2, vt1);  // top edges
         const T2 dl0 = sub2(vt0, vb0), dl1 = sub2(vt1, vb1);  // vertical edges at i0, i1
@@ -637,7 +678,8 @@ __global__ void __launch_bounds__(SWEEP_NT) sweep2_kernel(const SweepParams<T> a
     }
   }
   if constexpr (REDUCE) {
-    block_reduce_finish<SWEEP_NT>(dot0, dot1, a.partials, a.ticket, a.sc, a.finish, a.out_value);
+    block_reduce_finish<SWEEP_NT>(dot0, dot1, a.partials, a.ticket, a.sc, a.finish, a.out_value,
+                                  a.tag);
   }
 }
 

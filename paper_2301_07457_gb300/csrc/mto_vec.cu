@@ -83,29 +83,52 @@ __global__ void jacobi0_coarse_kernel(Grid g, const typename V2<T>::t* __restric
   }
 }
 
+// r -= alpha q, |r|^2 (FIN_UPDATE, which marks the x step as pending), and
+// the float32 copy of r.  x += alpha p happens in the next K p sweep or in
+// x_step_kernel after the loop.
 __global__ void __launch_bounds__(VEC_NT)
-    update_kernel(long long n, double2* __restrict__ x, double2* __restrict__ r,
-                  float2* __restrict__ r32, const double2* __restrict__ p,
+    update_kernel(long long n, double2* __restrict__ r, float2* __restrict__ r32,
                   const double2* __restrict__ q, double* partials, unsigned* ticket,
                   DevScalars* sc) {
   pdl_wait();
   if (sc->done != RUNNING) return;
   const double alpha = sc->alpha;
   double acc = 0.0;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const double2 pp = p[k], qq = q[k];
-    double2 xx = x[k], rr = r[k];
-    xx.x += alpha * pp.x;
-    xx.y += alpha * pp.y;
+  auto one = [&](long long k, const double2 qq, double2 rr) {
     rr.x -= alpha * qq.x;
     rr.y -= alpha * qq.y;
-    x[k] = xx;
     r[k] = rr;
     if (r32 != nullptr) r32[k] = make_float2(d2f_rn(rr.x), d2f_rn(rr.y));
     acc = fma(rr.x, rr.x, fma(rr.y, rr.y, acc));
+  };
+  // Two nodes per pass with the loads issued first (more bytes in flight).
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + stride < n; k += 2 * stride) {
+    const double2 q0 = q[k], r0 = r[k], q1 = q[k + stride], r1 = r[k + stride];
+    one(k, q0, r0);
+    one(k + stride, q1, r1);
   }
+  if (k < n) one(k, q[k], r[k]);
   block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, FIN_UPDATE, nullptr);
+}
+
+// The pending x step after the loop: x += alpha p[p_par] when x_lag.
+__global__ void __launch_bounds__(VEC_NT)
+    x_step_kernel(long long n, double2* __restrict__ x, const double2* __restrict__ p0,
+                  const double2* __restrict__ p1, const DevScalars* sc) {
+  pdl_wait();
+  if (sc->x_lag == 0) return;
+  const double alpha = sc->alpha;
+  const double2* __restrict__ p = sc->p_par ? p1 : p0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double2 pp = p[k];
+    double2 xx = x[k];
+    xx.x = fma(alpha, pp.x, xx.x);
+    xx.y = fma(alpha, pp.y, xx.y);
+    x[k] = xx;
+  }
 }
 
 __global__ void __launch_bounds__(VEC_NT)
@@ -288,10 +311,15 @@ template cudaError_t launch_jacobi0_coarse<double>(const Grid&, const double2*, 
 template cudaError_t launch_jacobi0_coarse<float>(const Grid&, const float2*, const float2*,
                                                   float2*, DevScalars*, int, cudaStream_t);
 
-cudaError_t launch_update(const Grid& g, double2* x, double2* r, float2* r32, const double2* p,
-                          const double2* q, double* partials, unsigned* ticket, DevScalars* sc,
-                          int nblocks, cudaStream_t s) {
-  return launch_pdl(update_kernel, nblocks, VEC_NT, 0, s, g.size(), x, r, r32, p, q, partials, ticket, sc);
+cudaError_t launch_update(const Grid& g, double2* r, float2* r32, const double2* q,
+                          double* partials, unsigned* ticket, DevScalars* sc, int nblocks,
+                          cudaStream_t s) {
+  return launch_pdl(update_kernel, nblocks, VEC_NT, 0, s, g.size(), r, r32, q, partials, ticket, sc);
+}
+
+cudaError_t launch_x_step(const Grid& g, double2* x, const double2* p0, const double2* p1,
+                          const DevScalars* sc, int nblocks, cudaStream_t s) {
+  return launch_pdl(x_step_kernel, nblocks, VEC_NT, 0, s, g.size(), x, p0, p1, sc);
 }
 
 cudaError_t launch_dot(long long n, const double2* a, const double2* b, double* partials,
