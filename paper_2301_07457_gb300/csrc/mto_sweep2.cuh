@@ -307,28 +307,21 @@ __device__ __forceinline__ void fbf_winv_own(float ebl, float eb0, float eb1, fl
 __device__ __forceinline__ float bf_lo(__nv_bfloat162 v) { return __low2float(v); }
 __device__ __forceinline__ float bf_hi(__nv_bfloat162 v) { return __high2float(v); }
 
-// Two resident blocks per SM (at most 128 registers per thread): one full
-// wave is then 16 warps per SM, which the launch shapes assume.
+// One warp task of a two-column sweep: strip and chunk from the task index
+// wg (all 32 lanes call it together).  Dot-product contributions accumulate
+// into dot0 / dot1; the caller reduces them.
 template <typename T, int SRC, int MODE, bool DOT, typename ZT, int PF>
-__global__ void __launch_bounds__(SWEEP_NT, 2) sweep2_kernel(const SweepParams<T> a) {
+__device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int lane, double& dot0,
+                                            double& dot1) {
   using T2 = typename V2<T>::t;
   using S2 = Sweep2<T, SRC, MODE, DOT, ZT>;
   using VR = typename S2::VR;
   using ER = typename S2::ER;
   using NR = typename S2::NR;
-  constexpr bool REDUCE = DOT || MODE == MODE_RESID || MODE == MODE_KP;
   constexpr bool FBF = SRC == SRC_FINEBF;
   constexpr bool FBF0 = FBF && MODE == MODE_SMOOTH0;
-  pdl_wait();
-  if (a.sc != nullptr && a.gate) {
-    if (a.sc->done != RUNNING) return;  // uniform over the grid
-    if (a.replace_gate && (a.sc->rr_every <= 0 || (a.sc->iter % a.sc->rr_every) != 0)) return;
-  }
-  const int lane = threadIdx.x & 31;
-  const int wg = blockIdx.x * (SWEEP_NT / 32) + (threadIdx.x >> 5);
   const int strip = wg % a.nstrips;
   const int chunk = wg / a.nstrips;
-  double dot0 = 0.0, dot1 = 0.0;
   T beta = T(0);
   if constexpr (MODE == MODE_KP) beta = T(a.sc->beta);
   bool vzero = false;
@@ -677,6 +670,22 @@ __global__ void __launch_bounds__(SWEEP_NT, 2) sweep2_kernel(const SweepParams<T
       }
     }
   }
+}
+
+// Two resident blocks per SM (at most 128 registers per thread): one full
+// wave is then 16 warps per SM, which the launch shapes assume.
+template <typename T, int SRC, int MODE, bool DOT, typename ZT, int PF>
+__global__ void __launch_bounds__(SWEEP_NT, 2) sweep2_kernel(const SweepParams<T> a) {
+  constexpr bool REDUCE = DOT || MODE == MODE_RESID || MODE == MODE_KP;
+  pdl_wait();
+  if (a.sc != nullptr && a.gate) {
+    if (a.sc->done != RUNNING) return;  // uniform over the grid
+    if (a.replace_gate && (a.sc->rr_every <= 0 || (a.sc->iter % a.sc->rr_every) != 0)) return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * (SWEEP_NT / 32) + (threadIdx.x >> 5);
+  double dot0 = 0.0, dot1 = 0.0;
+  sweep2_warp<T, SRC, MODE, DOT, ZT, PF>(a, wg, lane, dot0, dot1);
   if constexpr (REDUCE) {
     block_reduce_finish<SWEEP_NT>(dot0, dot1, a.partials, a.ticket, a.sc, a.finish, a.out_value,
                                   a.tag);

@@ -23,8 +23,11 @@ SweepShape sweep_shape(const Grid& g, int mode, int target_warps, int cols) {
     sh.nstrips = cols == 2 ? (g.nx + 2 + SWEEP2_STRIDE - 1) / SWEEP2_STRIDE
                            : (g.nx + 1 + SWEEP_STRIDE - 1) / SWEEP_STRIDE;
     const int want = target_warps / sh.nstrips > 1 ? target_warps / sh.nstrips : 1;
+    // One row per task on small levels: with the halo step, two steps whose
+    // loads all fit the lookahead ring, so the sweep costs one memory round
+    // trip instead of two.
     int h = (g.ny + 1 + want - 1) / want;
-    h = h < 2 ? 2 : (h > 64 ? 64 : h);
+    h = h < 1 ? 1 : (h > 64 ? 64 : h);
     sh.H = h;
     sh.nchunks = (g.ny + 1 + h - 1) / h;
   }

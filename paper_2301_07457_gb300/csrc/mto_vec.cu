@@ -1,6 +1,7 @@
 // Pointwise kernels of the PCG recurrence (Alg. 2), the first smoothing sweep
 // from a zero iterate (Sec. 2.3 with x_0 = 0), layout conversions and the
 // coarsest-grid solve of Alg. 1 (l = 0) as a dense product with K_0^-1.
+#include "mto_gemv.cuh"
 #include "mto_launch.h"
 
 namespace mto {
@@ -209,37 +210,25 @@ __global__ void unpack_elems_kernel(Grid g, const double* __restrict__ src, doub
 }
 
 // One warp per row of K_0^-1; every block stages the free coarse right-hand
-// side in shared memory first.  free_idx[k] = scalar index (2 * node offset +
-// component) of free DOF k in the padded level array.
+// side in shared memory first (mto_gemv.cuh).
 constexpr int GEMV_NT = 256;
-constexpr int GEMV_MAXN = 4096;
 
 template <typename T>
 __global__ void __launch_bounds__(GEMV_NT)
     coarsest_gemv_kernel(int n, const int* __restrict__ free_idx, const double* __restrict__ Kinv,
                          const T* __restrict__ b, T* __restrict__ z, const DevScalars* sc) {
+  // K_0^-1 and the DOF map are set up once per design: load this warp's row
+  // before waiting for the previous kernel (programmatic dependent launch).
+  const int row = blockIdx.x * (GEMV_NT / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  double kreg[GEMV_REG_COLS];
+  int zidx = 0;
+  if (row < n) gemv_prefetch(n, row, lane, free_idx, Kinv, kreg, zidx);
   pdl_wait();
   if (stop_now(sc)) return;
   extern __shared__ double bs[];
-  for (int k = threadIdx.x; k < n; k += GEMV_NT) bs[k] = (double)b[free_idx[k]];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (GEMV_NT / 32) + (threadIdx.x >> 5);
-  if (row >= n) return;
-  const double* kr = Kinv + (long long)row * n;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // independent chains
-  int k = lane;
-  for (; k + 96 < n; k += 128) {
-    a0 += kr[k] * bs[k];
-    a1 += kr[k + 32] * bs[k + 32];
-    a2 += kr[k + 64] * bs[k + 64];
-    a3 += kr[k + 96] * bs[k + 96];
-  }
-  for (; k < n; k += 32) a0 += kr[k] * bs[k];
-  double acc = (a0 + a1) + (a2 + a3);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) z[free_idx[row]] = (T)acc;
+  gemv_stage<T>(n, free_idx, b, bs);
+  if (row < n) gemv_row<T>(n, row, lane, free_idx, Kinv, bs, z, kreg, zidx);
 }
 
 // PCG scalars of a fresh solve (kernel parameters, so the launch can live in a
