@@ -89,17 +89,25 @@ __global__ void moments_from_fine_kernel(Grid gc, Grid gf, const double* __restr
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const int I = (int)(t % gc.nx), J = (int)(t / gc.nx);
-    Mom P = {0, 0, 0, 0, 0, 0};
-    double Emean = 0.0;
+    // Children of constant modulus at xi, eta = +-1/2: the shift-and-scale
+    // rule of accum_child in closed form, M00 = S/4, M10 = X/8, M01 = Y/8,
+    // M20 = M02 = M00/3, M11 = Z/16 (S, X, Y, Z: sums of the child moduli
+    // with signs 1, s_x, s_y, s_x s_y).
+    const long long kf = gf.at(2 * I, 2 * J);
+    double e[2][2];
     for (int cy = 0; cy < 2; ++cy)
       for (int cx = 0; cx < 2; ++cx) {
-        const long long kf = gf.at(2 * I + cx, 2 * J + cy);
-        const double E = Ebf ? (double)__bfloat162float(Ebf[kf]) : E64[kf];
-        const Mom c = {E, 0.0, 0.0, E / 3.0, E / 3.0, 0.0};
-        accum_child(P, c, 2.0 * cx - 1.0, 2.0 * cy - 1.0);
-        Emean += 0.25 * E;
+        const long long k = kf + (long long)cy * gf.pitch + cx;
+        e[cy][cx] = Ebf ? (double)__bfloat162float(Ebf[k]) : E64[k];
       }
-    if (redisc) P = {Emean, 0.0, 0.0, Emean / 3.0, Emean / 3.0, 0.0};
+    const double S = (e[0][0] + e[0][1]) + (e[1][0] + e[1][1]);
+    const double M00 = 0.25 * S;
+    Mom P = {M00, 0.0, 0.0, M00 / 3.0, M00 / 3.0, 0.0};
+    if (!redisc) {
+      P.m10 = 0.125 * ((e[0][1] + e[1][1]) - (e[0][0] + e[1][0]));
+      P.m01 = 0.125 * ((e[1][0] + e[1][1]) - (e[0][0] + e[0][1]));
+      P.m11 = 0.0625 * ((e[0][0] + e[1][1]) - (e[0][1] + e[1][0]));
+    }
     store_mom(mom, gc.size(), gc.at(I, J), P);
   }
 }
@@ -150,46 +158,53 @@ __global__ void coefs_kernel(Grid g, const double* __restrict__ mom, double nu, 
 // Diagonal of an element matrix J^T A J at local node q (0 BL, 1 BR, 2 TR, 3 TL):
 // J column of u_x at q is (s1, s3, 0, 0, s2), of u_y is (0, 0, s2, s3, s1), with
 // s1 = (-1, 1, 1, -1), s2 = (-1, -1, 1, 1), s3 = (1, -1, 1, -1); s1 s3 = s2, s2 s3 = s1.
-__device__ __forceinline__ void elem_diag(const double A[NCOEF], int q, double& dx, double& dy) {
-  const double s1 = (q == 1 || q == 2) ? 1.0 : -1.0;
-  const double s2 = (q >= 2) ? 1.0 : -1.0;
-  dx += A[0] + A[2] + A[10] + 2.0 * s2 * A[1] + 2.0 * s1 * A[11];
-  dy += A[3] + A[5] + A[10] + 2.0 * s1 * A[4] + 2.0 * s2 * A[12];
+template <typename C>
+__device__ __forceinline__ void elem_diag(const C A[NCOEF], int q, C& dx, C& dy) {
+  const C s1 = (q == 1 || q == 2) ? C(1) : C(-1);
+  const C s2 = (q >= 2) ? C(1) : C(-1);
+  dx += A[0] + A[2] + A[10] + C(2) * s2 * A[1] + C(2) * s1 * A[11];
+  dy += A[3] + A[5] + A[10] + C(2) * s1 * A[4] + C(2) * s2 * A[12];
 }
 
-// Coefficients of element k from the float64 moments (zero for ghost elements).
+// Coefficients of element k from the float64 moments (zero for ghost
+// elements), in the precision C of the level (float32 levels convert the
+// moments on the integer pipe and stay off the FP64 pipe).
+template <typename C>
 __device__ __forceinline__ void coefs_at(const double* __restrict__ mom, long long s, long long k,
-                                         double kap, double nu, double gs, double A[NCOEF]) {
-  double m[NMOM];
+                                         C kap, C nu, C gs, C A[NCOEF]) {
+  C m[NMOM];
 #pragma unroll
-  for (int c = 0; c < NMOM; ++c) m[c] = kap * mom[c * s + k];
-  coefs_from_kmom<double>(m, nu, gs, A);
+  for (int c = 0; c < NMOM; ++c) {
+    if constexpr (sizeof(C) == 4) m[c] = kap * d2f_rn(mom[c * s + k]);
+    else m[c] = kap * mom[c * s + k];
+  }
+  coefs_from_kmom<C>(m, nu, gs, A);
 }
 
-// w / D per DOF of a coarse level, from the float64 moments of its elements.
+// w / D per DOF of a coarse level, from the moments of its elements.
 template <typename T>
 __global__ void coarse_invd_kernel(Grid g, const double* __restrict__ mom, double nu, double omega,
                                    typename V2<T>::t* __restrict__ invd2) {
   const long long n = (long long)(g.nx + 1) * (g.ny + 1);
   const long long s = g.size();
-  const double kap = 1.0 / (4.0 * (1.0 - nu * nu)), gs = 0.5 * (1.0 - nu);
+  const T kap = T(1.0 / (4.0 * (1.0 - nu * nu))), gs = T(0.5 * (1.0 - nu)), nut = T(nu);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
     const long long k = g.at(i, j);
     typename V2<T>::t out = mk2<T>(T(0), T(0));
     if (!g.is_fixed(i, j)) {
-      double dx = 0.0, dy = 0.0, A[NCOEF];
+      T dx = T(0), dy = T(0), A[NCOEF];
       // Ghost elements have zero moments, so all four may be visited.
-      coefs_at(mom, s, k - g.pitch - 1, kap, nu, gs, A);
-      elem_diag(A, 2, dx, dy);  // element (i-1, j-1): node is TR
-      coefs_at(mom, s, k - g.pitch, kap, nu, gs, A);
-      elem_diag(A, 3, dx, dy);  // element (i, j-1): TL
-      coefs_at(mom, s, k - 1, kap, nu, gs, A);
-      elem_diag(A, 1, dx, dy);  // element (i-1, j): BR
-      coefs_at(mom, s, k, kap, nu, gs, A);
-      elem_diag(A, 0, dx, dy);  // element (i, j): BL
-      out = mk2<T>(T(omega / dx), T(omega / dy));
+      coefs_at<T>(mom, s, k - g.pitch - 1, kap, nut, gs, A);
+      elem_diag<T>(A, 2, dx, dy);  // element (i-1, j-1): node is TR
+      coefs_at<T>(mom, s, k - g.pitch, kap, nut, gs, A);
+      elem_diag<T>(A, 3, dx, dy);  // element (i, j-1): TL
+      coefs_at<T>(mom, s, k - 1, kap, nut, gs, A);
+      elem_diag<T>(A, 1, dx, dy);  // element (i-1, j): BR
+      coefs_at<T>(mom, s, k, kap, nut, gs, A);
+      elem_diag<T>(A, 0, dx, dy);  // element (i, j): BL
+      out = mk2<T>(T(omega) / dx, T(omega) / dy);
     }
     invd2[k] = out;
   }
@@ -270,52 +285,68 @@ __global__ void band_assemble_kernel(Grid g, const double* __restrict__ coef,
   }
 }
 
+// Right-looking band Cholesky (Alg. 3) with the next pivot taken off the
+// critical path: one block of sixteen warps.  Step k scales column k by the
+// pivot 1/L_kk computed in step k - 1, then updates the trailing triangle;
+// warp 0 updates only the next diagonal entry (pair (0, 0)) and at once
+// forms the next pivot (a reciprocal square root on the FP64 pipe), while
+// warps 1-15 share the other pairs.  Two barriers per column.
 constexpr int CHOL_NT = 512;
 
-// Right-looking Cholesky (Alg. 3, textbook indices) of the band matrix in
-// lower band storage B[i * (bw + 1) + d] = A[i][i - d], one block.  A band
-// matrix keeps its factor inside the band.  With SMEM the band lives in shared
-// memory for the whole factorisation.  Also writes 1 / L_ii.
 template <bool SMEM>
 __global__ void __launch_bounds__(CHOL_NT)
     cholesky_band_kernel(int n, int bw, double* Bg, double* invL, int* err) {
   extern __shared__ double dyn[];
-  __shared__ double piv;
+  __shared__ double piv_s;
   const int W = bw + 1;
   double* B = SMEM ? dyn : Bg;
   short2* pairs = reinterpret_cast<short2*>(SMEM ? dyn + (size_t)n * W : dyn);
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (SMEM)
-    for (int t = threadIdx.x; t < n * W; t += CHOL_NT) B[t] = Bg[t];
-  for (int ii = threadIdx.x; ii < bw; ii += CHOL_NT)
+    for (int t = tid; t < n * W; t += CHOL_NT) B[t] = Bg[t];
+  for (int ii = tid; ii < bw; ii += CHOL_NT)
     for (int jj = 0; jj <= ii; ++jj) pairs[ii * (ii + 1) / 2 + jj] = make_short2((short)ii, (short)jj);
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      double d = B[(size_t)k * W];
-      if (!(d > 0.0) || !(d < 1.0e300)) {
-        *err = 1;
-        d = 1.0;
-      }
-      d = sqrt(d);
-      B[(size_t)k * W] = d;
-      piv = 1.0 / d;
-      invL[k] = piv;
+  auto pivot = [&](int k) {
+    double d = B[(size_t)k * W];
+    if (!(d > 0.0) || !(d < 1.0e300)) {
+      *err = 1;
+      d = 1.0;
     }
-    __syncthreads();
+    const double r = rsqrt(d);  // 1 / L_kk in one sequence (no separate division)
+    B[(size_t)k * W] = d * r;
+    piv_s = r;
+    invL[k] = r;
+  };
+  if (tid == 0) pivot(0);
+  __syncthreads();
+  const int np_full = bw * (bw + 1) / 2;
+  for (int k = 0; k < n; ++k) {
+    const double piv = piv_s;
     const int last = min(n - 1, k + bw);
-    for (int i = k + 1 + threadIdx.x; i <= last; i += CHOL_NT) B[(size_t)i * W + (i - k)] *= piv;
-    __syncthreads();
     const int m = last - k;
-    const int np = m * (m + 1) / 2;
-    for (int t = threadIdx.x; t < np; t += CHOL_NT) {
-      const short2 pr = pairs[t];
-      const int i = k + 1 + pr.x, j = k + 1 + pr.y;
-      B[(size_t)i * W + (i - j)] -= B[(size_t)i * W + (i - k)] * B[(size_t)j * W + (j - k)];
+    for (int i = k + 1 + tid; i <= last; i += CHOL_NT) B[(size_t)i * W + (i - k)] *= piv;
+    __syncthreads();
+    if (warp == 0) {
+      if (tid == 0 && m > 0) {
+        const double l = B[(size_t)(k + 1) * W + 1];
+        B[(size_t)(k + 1) * W] -= l * l;  // pair (0, 0): the next diagonal entry
+        pivot(k + 1);
+      }
+    } else {
+      const int np = m * (m + 1) / 2;
+      for (int t = 1 + (tid - 32); t < np_full; t += CHOL_NT - 32) {
+        const short2 pr = pairs[t];
+        if (pr.x >= m) continue;  // rows beyond the matrix near the end
+        const int i = k + 1 + pr.x, j = k + 1 + pr.y;
+        B[(size_t)i * W + (i - j)] -= B[(size_t)i * W + (i - k)] * B[(size_t)j * W + (j - k)];
+      }
+      (void)np;
     }
     __syncthreads();
   }
   if (SMEM)
-    for (int t = threadIdx.x; t < n * W; t += CHOL_NT) Bg[t] = B[t];
+    for (int t = tid; t < n * W; t += CHOL_NT) Bg[t] = B[t];
 }
 
 // K_0^-1 by columns: L y = e_j (forward), then L^T x = y (backward), column j
@@ -507,9 +538,88 @@ static int max_dyn_smem() {
   return v;
 }
 
+// K_0^-1 by columns with column-oriented (axpy) substitution: one warp per
+// column j, four columns per block.  Forward, L y = e_j: at row k the warp
+// has the running sum acc_k = sum_{m<k} L_km y_m ready, forms
+// y_k = (delta_kj - acc_k) / L_kk (every lane the same value), and adds
+// L_rk y_k to the sums of the next bw rows r.  The sums of a window of
+// 32 NS rows live in registers: row r in lane r mod 32, slot (r / 32) mod NS,
+// so a row's sum is broadcast by one shuffle and each step costs one FP64
+// operation per slot and lane (no reduction).  Backward, L^T x = y, runs the
+// same way from the last row up.  Column j of K_0^-1 is row j (symmetric).
+// With LSMEM the band factor is staged in shared memory for the block; each
+// warp keeps its y in shared memory between the two passes.
+constexpr int INVA_WARPS = 4;
+
+template <bool LSMEM, int NS>
+__global__ void __launch_bounds__(32 * INVA_WARPS)
+    inverse_axpy_kernel(int n, int bw, const double* __restrict__ Lg, const double* __restrict__ invL,
+                        double* __restrict__ Kinv) {
+  extern __shared__ double dyn[];
+  constexpr int WIN = 32 * NS;
+  const int W = bw + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* L = Lg;
+  if (LSMEM) {
+    for (int q = threadIdx.x; q < n * W; q += blockDim.x) dyn[q] = Lg[q];
+    L = dyn;
+  }
+  double* ybuf = dyn + (LSMEM ? (size_t)n * W : 0) + (size_t)warp * n;
+  __syncthreads();
+  const int j = blockIdx.x * INVA_WARPS + warp;
+  if (j >= n) return;  // no block-level synchronisation below
+  double acc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+  // Sum of row r, held by lane r % 32 in slot (r / 32) % NS, broadcast.
+  auto take = [&](int r) -> double {
+    const int sr = (r >> 5) & (NS - 1);
+    double mine = acc[0];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) mine = sr == s ? acc[s] : mine;
+    const double v = __shfl_sync(0xffffffffu, mine, r & 31);
+    if (lane == (r & 31)) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (sr == s) acc[s] = 0.0;  // the slot is reused for row r + WIN
+    }
+    return v;
+  };
+  for (int k = j; k < n; ++k) {
+    const double il = invL[k];
+    const double ak = take(k);
+    const double y = k == j ? fma(-ak, il, il) : -ak * il;
+    if (lane == 0) ybuf[k] = y;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int o = (lane + 32 * s - (k + 1)) & (WIN - 1);  // row k + 1 + o
+      const int r = k + 1 + o;
+      if (o < bw && r < n) acc[s] = fma(L[(size_t)r * W + 1 + o], y, acc[s]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+  double* row = Kinv + (size_t)j * n;
+  for (int i = n - 1; i >= 0; --i) {
+    const double il = invL[i];
+    const double yi = i >= j ? ybuf[i] : 0.0;
+    const double ai = take(i);
+    const double x = (yi - ai) * il;
+    if (lane == 0) row[i] = x;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int o = ((i - 1) - (lane + 32 * s)) & (WIN - 1);  // row i - 1 - o
+      const int r = i - 1 - o;
+      if (o < bw && r >= 0) acc[s] = fma(L[(size_t)i * W + 1 + o], x, acc[s]);
+    }
+  }
+}
+
 struct CholPlan {
-  size_t pairs, band, win;
-  bool band_smem, inv_smem;
+  size_t pairs, band, win, ybuf;
+  bool band_smem, inv_smem, axpy_smem;
+  int slots;  // register slots of the axpy inverse (0: use inverse_cols_kernel)
 };
 
 static CholPlan chol_plan(int n, int bw) {
@@ -518,10 +628,20 @@ static CholPlan chol_plan(int n, int bw) {
   p.pairs = sizeof(short2) * (size_t)bw * (bw + 1) / 2 + 16;
   p.band = sizeof(double) * (size_t)n * W;
   p.win = sizeof(double) * (size_t)W * 32;
+  p.ybuf = sizeof(double) * (size_t)n * INVA_WARPS;
   const int cap = max_dyn_smem();
   p.band_smem = p.band + p.pairs <= (size_t)cap;
   p.inv_smem = p.band + p.win <= (size_t)cap;
+  p.axpy_smem = p.band + p.ybuf <= (size_t)cap;
+  p.slots = bw < 64 ? 2 : (bw < 128 ? 4 : 0);
+  if (p.ybuf > (size_t)cap) p.slots = 0;
   return p;
+}
+
+template <bool LSMEM, int NS> static cudaError_t set_axpy_smem(size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(inverse_axpy_kernel<LSMEM, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
 }
 
 cudaError_t prepare_cholesky_inverse(int n, int bw) {
@@ -534,6 +654,12 @@ cudaError_t prepare_cholesky_inverse(int n, int bw) {
     e = cudaFuncSetAttribute(cholesky_band_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pl.pairs);
   if (e != cudaSuccess) return e;
+  if (pl.slots == 2) {
+    return pl.axpy_smem ? set_axpy_smem<true, 2>(pl.band + pl.ybuf) : set_axpy_smem<false, 2>(pl.ybuf);
+  }
+  if (pl.slots == 4) {
+    return pl.axpy_smem ? set_axpy_smem<true, 4>(pl.band + pl.ybuf) : set_axpy_smem<false, 4>(pl.ybuf);
+  }
   if (pl.inv_smem)
     e = cudaFuncSetAttribute(inverse_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(pl.band + pl.win));
@@ -553,6 +679,18 @@ cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, dou
     cholesky_band_kernel<false><<<1, CHOL_NT, pl.pairs, s>>>(n, bw, Kb, invL, err_flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (pl.slots) {
+    const int ab = (n + INVA_WARPS - 1) / INVA_WARPS;
+    const size_t sm = (pl.axpy_smem ? pl.band : 0) + pl.ybuf;
+    if (pl.slots == 2) {
+      if (pl.axpy_smem) inverse_axpy_kernel<true, 2><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
+      else inverse_axpy_kernel<false, 2><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
+    } else {
+      if (pl.axpy_smem) inverse_axpy_kernel<true, 4><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
+      else inverse_axpy_kernel<false, 4><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
+    }
+    return cudaGetLastError();
+  }
   const int blocks = (n + INV_COLS - 1) / INV_COLS;
   if (pl.inv_smem)
     inverse_cols_kernel<true><<<blocks, 32, pl.band + pl.win, s>>>(n, bw, Kb, invL, Kinv);
