@@ -21,7 +21,7 @@ constexpr int NMOM = 6;
 // Geometry of one grid level in the padded layout shared by its node and
 // element arrays.  Node (i, j) and element (i, j) both live at
 //   (j + 1) * pitch + OFFX + i,
-// for i in [-1, nx+1], j in [-1, ny+2]; everything outside the real mesh
+// for i in [-OFFX, nx+65], j in [-1, ny+2]; everything outside the real mesh
 // (ghost ring, right padding, extra rows) is zero and never written, so the
 // stencil needs no bounds tests.
 struct Grid {

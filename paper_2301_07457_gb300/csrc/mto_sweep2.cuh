@@ -560,7 +560,12 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
         const bool act0 = inb0 && !cfix0 && !rfix, act1 = inb1 && !cfix1 && !rfix;
 
         if constexpr (MODE == MODE_APPLY) {
-          st_pair(a.out, k, act0 ? kv0 : zero2, act1 ? kv1 : zero2, inb0, inb1);
+          if constexpr (sizeof(T) == 4) {  // mask by multiplication (FMA pipe, values finite)
+            const T m0 = act0 ? T(1) : T(0), m1 = act1 ? T(1) : T(0);
+            st_pair(a.out, k, mk2<T>(kv0.x * m0, kv0.y * m0), mk2<T>(kv1.x * m1, kv1.y * m1), inb0, inb1);
+          } else {
+            st_pair(a.out, k, act0 ? kv0 : zero2, act1 ? kv1 : zero2, inb0, inb1);
+          }
         } else if constexpr (MODE == MODE_RESID) {
           const T2 r0 = act0 ? sub2(cur.n.b0, kv0) : zero2;
           const T2 r1 = act1 ? sub2(cur.n.b1, kv1) : zero2;
@@ -590,8 +595,11 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
               d0 = mk2<T>(T(cur.n.d1.x), T(cur.n.d1.x));
               d1 = mk2<T>(T(cur.n.d1.y), T(cur.n.d1.y));
             } else if constexpr (FBF) {
+              // D from the moduli is zero on ghost nodes: mask w / D itself.
               float w0f, w1f;
               fbf_winv(ep0, ep1, ec0, ec1, float(a.wdiag), w0f, w1f);
+              w0f = act0 ? w0f : 0.f;
+              w1f = act1 ? w1f : 0.f;
               d0 = mk2<T>(w0f, w0f);
               d1 = mk2<T>(w1f, w1f);
             } else {
@@ -599,24 +607,28 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
               d1 = cur.n.d21;
             }
           }
-          const T2 z0 = act0 ? mk2<T>(vb0.x + d0.x * (b0.x - kv0.x), vb0.y + d0.y * (b0.y - kv0.y)) : zero2;
-          const T2 z1 = act1 ? mk2<T>(vb1.x + d1.x * (b1.x - kv1.x), vb1.y + d1.y * (b1.y - kv1.y)) : zero2;
+          // w / D, the marched v and b all vanish on clamped and ghost nodes,
+          // so z does too without a select.
+          const T2 z0 = mk2<T>(vb0.x + d0.x * (b0.x - kv0.x), vb0.y + d0.y * (b0.y - kv0.y));
+          const T2 z1 = mk2<T>(vb1.x + d1.x * (b1.x - kv1.x), vb1.y + d1.y * (b1.y - kv1.y));
           st_pair(a.out, k, z0, z1, inb0, inb1);
           if constexpr (DOT) {
-            if (act0) {
+            // Inactive nodes contribute 0 (z and r vanish there).
+            if (inb0) {
               const double zx = to_f64(z0.x), zy = to_f64(z0.y);
               dot0 = fma(zx, dcur.rd0.x, fma(zy, dcur.rd0.y, dot0));
               if (a.qdot != nullptr) dot1 = fma(zx, dcur.qd0.x, fma(zy, dcur.qd0.y, dot1));
             }
-            if (act1) {
+            if (inb1) {
               const double zx = to_f64(z1.x), zy = to_f64(z1.y);
               dot0 = fma(zx, dcur.rd1.x, fma(zy, dcur.rd1.y, dot0));
               if (a.qdot != nullptr) dot1 = fma(zx, dcur.qd1.x, fma(zy, dcur.qd1.y, dot1));
             }
           }
         } else if constexpr (MODE == MODE_RESTRICT) {
-          const T2 r0 = act0 ? sub2(cur.n.b0, kv0) : zero2;
-          const T2 r1 = act1 ? sub2(cur.n.b1, kv1) : zero2;
+          const T m0 = act0 ? T(1) : T(0), m1 = act1 ? T(1) : T(0);  // multiplicative masks
+          const T2 r0 = mk2<T>((cur.n.b0.x - kv0.x) * m0, (cur.n.b0.y - kv0.y) * m0);
+          const T2 r1 = mk2<T>((cur.n.b1.x - kv1.x) * m1, (cur.n.b1.y - kv1.y) * m1);
           // Horizontal full weighting (1/2, 1, 1/2) onto coarse column
           // I = i0 / 2 (lanes 1..30), then vertical accumulation along the
           // march over fine rows 2J - 1, 2J, 2J + 1.
