@@ -147,6 +147,7 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
   BK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
   mto_status st = MTO_OK;
   long long fixed = 0;
+  g_pdl = false;  // concurrent branches: no early-waiting blocks (see launch_pdl)
   cudaError_t ce = cudaEventRecord(b->fork, b->origin);
   for (int i = 0; i < n && st == MTO_OK && ce == cudaSuccess; ++i) {
     mto_ctx* c = b->ctx[i];
@@ -160,6 +161,7 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
     if (st == MTO_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[i], 0);
   }
   const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+  g_pdl = true;
   for (mto_ctx* c : b->ctx) c->cs = c->stream;
   if (st != MTO_OK || ce != cudaSuccess || ee != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);

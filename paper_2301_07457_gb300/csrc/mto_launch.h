@@ -8,9 +8,15 @@
 
 namespace mto {
 
+// Programmatic dependent launch for the launches of this thread (on by
+// default).  Batched graphs turn it off while they capture: there, a kernel
+// whose blocks wait early on SM slots would hold them from the other
+// problems' concurrent branches.
+extern thread_local bool g_pdl;
+
 // Launch a kernel that calls pdl_wait() first, allowing programmatic
 // dependent launch after the previous kernel on the stream (captured into
-// graphs as a programmatic edge).
+// graphs as a programmatic edge) while g_pdl is set.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
                        Args&&... args) {
@@ -23,7 +29,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t sme
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = g_pdl ? 1 : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
   return e != cudaSuccess ? e : cudaGetLastError();
 }

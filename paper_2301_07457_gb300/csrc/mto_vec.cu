@@ -6,6 +6,8 @@
 
 namespace mto {
 
+thread_local bool g_pdl = true;
+
 int vec_blocks(long long n, int num_sms) {
   long long b = (n + VEC_NT - 1) / VEC_NT;
   const long long cap = (long long)num_sms * 8;
