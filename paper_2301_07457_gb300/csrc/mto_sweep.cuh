@@ -122,6 +122,50 @@ template <typename T2> __device__ __forceinline__ T2 sub2(T2 a, T2 b) {
   a.y -= b.y;
   return a;
 }
+// float2 pairs use Blackwell's packed FP32 instructions (two correctly
+// rounded operations per instruction): the float32 sweeps are bound by
+// instruction issue, and most of their arithmetic treats u_x and u_y alike.
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+template <> __device__ __forceinline__ float2 add2<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+template <> __device__ __forceinline__ float2 sub2<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+// a * b + c per component (float2: one packed FMA).
+template <typename T2> __device__ __forceinline__ T2 fma2(T2 a, T2 b, T2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.y = fma(a.y, b.y, c.y);
+  return c;
+}
+template <> __device__ __forceinline__ float2 fma2<float2>(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(r);
+}
+template <typename T2> __device__ __forceinline__ T2 mul2(T2 a, T2 b) {
+  a.x *= b.x;
+  a.y *= b.y;
+  return a;
+}
+template <> __device__ __forceinline__ float2 mul2<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
 
 // Raw loads of the marched vector at one node (finished later, so that the
 // loads can be in flight while earlier steps compute).

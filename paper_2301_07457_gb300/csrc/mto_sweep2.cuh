@@ -464,10 +464,6 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
     for (int u = 0; u < PF; ++u)
       if (je0 + u <= je1) load_pack(ring[u], je0 + u, k0 + u * pitch);
     // Dot partners of node row je + 1 (dnext) and je (dcur).
-    DRaw2 dnext, dcur;
-    if constexpr (DOT) {
-      if (je0 + 1 <= je1) S2::load_d(a, k0 + pitch, dnext);
-    }
 
     long long k = k0;  // offset of node / element (i0, je)
     for (int jb = je0; jb <= je1; jb += PF) {
@@ -489,11 +485,9 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
             st_pair(a.xvec, k + pitch, x0, x1, own0, own1);
           }
         }
+        DRaw2 dcur;
         if constexpr (DOT) {
-          if (je > je0) {
-            dcur = dnext;
-            if (je + 1 <= je1) S2::load_d(a, k + pitch, dnext);
-          }
+          if (je > je0) S2::load_d(a, k, dcur);
         }
 
         // ---- top row je + 1 ----
@@ -527,31 +521,41 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
         T2 dl2;                                               // vertical edge at i0 + 2
         if constexpr (sizeof(T) == 8) dl2 = shfl_down2(dl0);  // a shuffle is cheaper than FP64
         else dl2 = sub2(vt2, vb2);
+        // Strain coordinates as component pairs: (c1, d1) = a + b,
+        // (c3, d3) = b - a, (c2, d2) = dl + dr, s = c2 + d1.
         Strain<T> w0, w1;
-        w0.c1 = ac0.x + bt0.x;
-        w0.c3 = bt0.x - ac0.x;
-        w0.d3 = bt0.y - ac0.y;
-        w0.d2 = dl0.y + dl1.y;
-        w0.s = (dl0.x + dl1.x) + (ac0.y + bt0.y);
-        w1.c1 = ac1.x + bt1.x;
-        w1.c3 = bt1.x - ac1.x;
-        w1.d3 = bt1.y - ac1.y;
-        w1.d2 = dl1.y + dl2.y;
-        w1.s = (dl1.x + dl2.x) + (ac1.y + bt1.y);
+        {
+          const T2 cd1 = add2(ac0, bt0), cd3 = sub2(bt0, ac0), cd2 = add2(dl0, dl1);
+          w0.c1 = cd1.x;
+          w0.c3 = cd3.x;
+          w0.d3 = cd3.y;
+          w0.d2 = cd2.y;
+          w0.s = cd2.x + cd1.y;
+        }
+        {
+          const T2 cd1 = add2(ac1, bt1), cd3 = sub2(bt1, ac1), cd2 = add2(dl1, dl2);
+          w1.c1 = cd1.x;
+          w1.c3 = cd3.x;
+          w1.d3 = cd3.y;
+          w1.d2 = cd2.y;
+          w1.s = cd2.x + cd1.y;
+        }
         const ER& ecur_raw = cur.e;  // element row je for every source but the bf16 moduli
         const Strain<T> t0 = S2::core(a, ecur_raw, 0, w0, T(ec0));
         const Strain<T> t1 = S2::core(a, ecur_raw, 1, w1, T(ec1));
         // ---- edge forces and node row je ----
-        const T2 ga0 = mk2<T>(t0.c1 - t0.c3, t0.s - t0.d3), gb0 = mk2<T>(t0.c1 + t0.c3, t0.s + t0.d3);
-        const T2 ga1 = mk2<T>(t1.c1 - t1.c3, t1.s - t1.d3), gb1 = mk2<T>(t1.c1 + t1.c3, t1.s + t1.d3);
+        const T2 p0 = mk2<T>(t0.c1, t0.s), m0p = mk2<T>(t0.c3, t0.d3);
+        const T2 p1 = mk2<T>(t1.c1, t1.s), m1p = mk2<T>(t1.c3, t1.d3);
+        const T2 ga0 = sub2(p0, m0p), gb0 = add2(p0, m0p);
+        const T2 ga1 = sub2(p1, m1p), gb1 = add2(p1, m1p);
         const T2 gs0 = mk2<T>(t0.s, t0.d2), gs1 = mk2<T>(t1.s, t1.d2);
         const T2 gh0 = add2(ga0, gbp0);  // horizontal edge i0 -> i1 of row je
         const T2 gh1 = add2(ga1, gbp1);  // i1 -> i0 + 2
         const T2 ghl = shfl_up2(gh1);    // i0 - 1 -> i0
         const T2 gv0 = add2(gs0, shfl_up2(gs1));  // vertical edge at i0, rows je -> je + 1
         const T2 gv1 = add2(gs0, gs1);            // at i1
-        const T2 kv0 = mk2<T>((ghl.x - gh0.x) + (gvp0.x - gv0.x), (ghl.y - gh0.y) + (gvp0.y - gv0.y));
-        const T2 kv1 = mk2<T>((gh0.x - gh1.x) + (gvp1.x - gv1.x), (gh0.y - gh1.y) + (gvp1.y - gv1.y));
+        const T2 kv0 = add2(sub2(ghl, gh0), sub2(gvp0, gv0));
+        const T2 kv1 = add2(sub2(gh0, gh1), sub2(gvp1, gv1));
 
         bool inrow = je > je0;
         if constexpr (MODE == MODE_RESTRICT) inrow = inrow && je <= g.ny;
@@ -609,8 +613,8 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
           }
           // w / D, the marched v and b all vanish on clamped and ghost nodes,
           // so z does too without a select.
-          const T2 z0 = mk2<T>(vb0.x + d0.x * (b0.x - kv0.x), vb0.y + d0.y * (b0.y - kv0.y));
-          const T2 z1 = mk2<T>(vb1.x + d1.x * (b1.x - kv1.x), vb1.y + d1.y * (b1.y - kv1.y));
+          const T2 z0 = fma2(d0, sub2(b0, kv0), vb0);
+          const T2 z1 = fma2(d1, sub2(b1, kv1), vb1);
           st_pair(a.out, k, z0, z1, inb0, inb1);
           if constexpr (DOT) {
             // Inactive nodes contribute 0 (z and r vanish there).
@@ -627,8 +631,8 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
           }
         } else if constexpr (MODE == MODE_RESTRICT) {
           const T m0 = act0 ? T(1) : T(0), m1 = act1 ? T(1) : T(0);  // multiplicative masks
-          const T2 r0 = mk2<T>((cur.n.b0.x - kv0.x) * m0, (cur.n.b0.y - kv0.y) * m0);
-          const T2 r1 = mk2<T>((cur.n.b1.x - kv1.x) * m1, (cur.n.b1.y - kv1.y) * m1);
+          const T2 r0 = mul2(sub2(cur.n.b0, kv0), mk2<T>(m0, m0));
+          const T2 r1 = mul2(sub2(cur.n.b1, kv1), mk2<T>(m1, m1));
           // Horizontal full weighting (1/2, 1, 1/2) onto coarse column
           // I = i0 / 2 (lanes 1..30), then vertical accumulation along the
           // march over fine rows 2J - 1, 2J, 2J + 1.
