@@ -511,18 +511,38 @@ mto_status enqueue_rhs_epilogue(mto_ctx* c, double* u_dev, int rhs_slot) {
   return MTO_OK;
 }
 
-mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
-                              double penal) {
-  const Grid& gf = c->lv[c->L].g;
-  const size_t nel = (size_t)c->nelx * c->nely;
-  if (c->xdes_cap < (size_t)n_phase * nel) return MTO_ERR_STATE;  // grown by the caller
+// Design parameters of the next set_design (host side only).
+void design_params(mto_ctx* c, int n_phase, const double* E_phase, double penal) {
   c->n_phase = n_phase;
   for (int i = 0; i < 16; ++i) c->ph.E[i] = i < n_phase ? E_phase[i] : 0.0;
   c->penal = penal;
   c->ipenal = (penal == std::floor(penal) && penal <= 16.0) ? (int)penal : -1;
+}
+
+// Finest moduli of element rows [j0, j1) from the design copy c->xdes.
+mto_status enqueue_modulus(mto_ctx* c, int j0, int j1) {
+  const Grid& gf = c->lv[c->L].g;
+  KL(launch_modulus(gf, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal, c->E64, c->Ebf, c->Ek4,
+                    c->kf64, c->cs, c->num_sms, j0, j1));
+  return MTO_OK;
+}
+
+// Everything of set_design after the finest moduli: the coarse hierarchy,
+// the smoothers' diagonals and the coarsest factor and inverse.
+mto_status enqueue_hierarchy(mto_ctx* c);
+
+mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
+                              double penal) {
+  const size_t nel = (size_t)c->nelx * c->nely;
+  if (c->xdes_cap < (size_t)n_phase * nel) return MTO_ERR_STATE;  // grown by the caller
+  design_params(c, n_phase, E_phase, penal);
   CK(cudaMemcpyAsync(c->xdes, x_dev, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice, c->cs));
-  KL(launch_modulus(gf, n_phase, c->xdes, c->ph, penal, c->ipenal, c->E64, c->Ebf, c->Ek4, c->kf64,
-                    c->cs, c->num_sms));
+  ST(enqueue_modulus(c, 0, c->nely));
+  return enqueue_hierarchy(c);
+}
+
+mto_status enqueue_hierarchy(mto_ctx* c) {
+  const Grid& gf = c->lv[c->L].g;
   if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->cs, c->num_sms));
   const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
   for (int l = c->L - 1; l >= 0; --l) {
@@ -713,6 +733,10 @@ void mto_destroy(mto_ctx* c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->ev_aux) cudaEventDestroy(c->ev_aux);
+  for (cudaEvent_t e : c->ev_chunk)
+    if (e) cudaEventDestroy(e);
+  if (c->aux) cudaStreamDestroy(c->aux);
   if (c->body_stream) cudaStreamDestroy(c->body_stream);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -738,6 +762,9 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
   CK(cudaEventCreate(&c->ev_a));
   CK(cudaEventCreate(&c->ev_b));
+  CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming));
+  for (cudaEvent_t& e : c->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CK(cudaMallocHost(&c->sc_host, sizeof(DevScalars)));
   CK(cudaMallocHost(&c->err_host, sizeof(int)));
   CK(cudaMallocHost(&c->rhs_stats_host, sizeof(RhsStats) * MAX_RHS));
@@ -927,7 +954,7 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
     return MTO_ERR_ARG;
   const size_t nel = (size_t)c->nelx * c->nely;
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
-  ST(grow(c, &c->hx, &c->hx_cap, (size_t)n_phase * nel));
+  ST(grow(c, &c->xdes, &c->xdes_cap, (size_t)n_phase * nel));
   size_t fcap = c->hf_cap;
   ST(grow(c, &c->hf, &c->hf_cap, (size_t)n_rhs * nd));
   ST(grow(c, &c->hu, &fcap, (size_t)n_rhs * nd));
@@ -936,20 +963,75 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
   c->hc_cap = (int)ccap;
   if (dcdx_host) ST(grow(c, &c->hg, &c->hg_cap, (size_t)n_phase * nel));
   ST(enter(c));
-  CK(cudaMemcpyAsync(c->hx, x_host, sizeof(double) * n_phase * nel, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->hf, f_host, sizeof(double) * n_rhs * nd, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemsetAsync(c->hu, 0, sizeof(double) * n_rhs * nd, c->stream));
   c->has_design = false;
-  ST(set_design_sync(c, n_phase, c->hx, E_phase, penal));
+  c->cs = c->stream;
+  const int nch = std::min(HOST_CHUNKS, c->nely);
+  auto rows = [&](int k) { return (int)((long long)c->nely * k / nch); };
+  // The side stream starts after all earlier work of the compute stream.
+  CK(cudaEventRecord(c->ev_aux, c->stream));
+  CK(cudaStreamWaitEvent(c->aux, c->ev_aux, 0));
+  // Design: x arrives in row chunks on the side stream and the moduli of a
+  // chunk are formed while the next one is in flight; f and the zero start
+  // follow on the side stream while the coarse hierarchy is built.
+  CK(cudaEventRecord(c->ev_a, c->stream));
+  design_params(c, n_phase, E_phase, penal);
+  for (int k = 0; k < nch; ++k) {
+    const int j0 = rows(k), j1 = rows(k + 1);
+    for (int p = 0; p < n_phase; ++p) {
+      const size_t off = (size_t)p * nel + (size_t)j0 * c->nelx;
+      CK(cudaMemcpyAsync(c->xdes + off, x_host + off, sizeof(double) * (size_t)(j1 - j0) * c->nelx,
+                         cudaMemcpyHostToDevice, c->aux));
+    }
+    CK(cudaEventRecord(c->ev_chunk[k], c->aux));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_chunk[k], 0));
+    ST(enqueue_modulus(c, j0, j1));
+  }
+  CK(cudaMemcpyAsync(c->hf, f_host, sizeof(double) * n_rhs * nd, cudaMemcpyHostToDevice, c->aux));
+  CK(cudaMemsetAsync(c->hu, 0, sizeof(double) * n_rhs * nd, c->aux));
+  CK(cudaEventRecord(c->ev_aux, c->aux));
+  ST(enqueue_hierarchy(c));
+  CK(cudaMemcpyAsync(c->err_host, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaEventRecord(c->ev_b, c->stream));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_aux, 0));  // f and u have landed
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaEventElapsedTime(&c->ms_setup, c->ev_a, c->ev_b));
+  if (*c->err_host) {
+    leave(c);
+    return MTO_ERR_BREAKDOWN;
+  }
+  c->has_design = true;
   const mto_status s = solve_rhs(c, n_rhs, c->hf, c->hu);
   if (s == MTO_ERR_CUDA || s == MTO_ERR_OOM || s == MTO_ERR_STATE) return s;
   c->cs = c->stream;
-  ST(enqueue_compliance(c, n_rhs, c->hf, c->hu, c->hc, dcdx_host ? c->hg : nullptr));
-  CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * n_rhs * nd, cudaMemcpyDeviceToHost, c->stream));
+  // Results: u leaves on the side stream while the compliance and the
+  // sensitivities are formed; the sensitivities leave in row chunks.
+  CK(cudaEventRecord(c->ev_aux, c->stream));
+  CK(cudaStreamWaitEvent(c->aux, c->ev_aux, 0));
+  CK(cudaMemcpyAsync(u_host, c->hu, sizeof(double) * n_rhs * nd, cudaMemcpyDeviceToHost, c->aux));
+  ST(enqueue_compliance(c, n_rhs, c->hf, c->hu, c->hc, nullptr));
   CK(cudaMemcpyAsync(compliance_host, c->hc, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, c->stream));
-  if (dcdx_host)
-    CK(cudaMemcpyAsync(dcdx_host, c->hg, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToHost,
-                       c->stream));
+  if (dcdx_host) {
+    const long long nn = (long long)(c->nelx + 1) * (c->nely + 1);
+    for (int k = 0; k < nch; ++k) {
+      for (int r = 0; r < n_rhs; ++r)
+        KL(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
+                              c->kf64, c->hu + 2 * nn * r, c->hg, r > 0, c->stream, c->num_sms,
+                              rows(k), rows(k + 1)));
+      CK(cudaEventRecord(c->ev_chunk[k], c->stream));
+    }
+    // Issued after every launch: a copy to pageable memory returns only
+    // when it is done.
+    for (int k = 0; k < nch; ++k) {
+      CK(cudaStreamWaitEvent(c->aux, c->ev_chunk[k], 0));
+      const int j0 = rows(k), j1 = rows(k + 1);
+      for (int p = 0; p < n_phase; ++p) {
+        const size_t off = (size_t)p * nel + (size_t)j0 * c->nelx;
+        CK(cudaMemcpyAsync(dcdx_host + off, c->hg + off, sizeof(double) * (size_t)(j1 - j0) * c->nelx,
+                           cudaMemcpyDeviceToHost, c->aux));
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(c->aux));
   CK(cudaStreamSynchronize(c->stream));
   ST(leave(c));
   if (stats) *stats = c->last;

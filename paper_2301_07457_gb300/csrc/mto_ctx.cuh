@@ -27,6 +27,10 @@ constexpr int MAX_RHS = 64;
 // per SM times the SM count (the default).
 constexpr int MAX_TARGET_WARPS_PER_SM = 128;
 
+// Row chunks in which mto_run_host moves x in and dC/dx out, each chunk's
+// transfer overlapping the kernels of its neighbours.
+constexpr int HOST_CHUNKS = 4;
+
 }  // namespace mto
 
 struct mto_ctx {
@@ -36,6 +40,10 @@ struct mto_ctx {
   // captures the body of the solver's device-side loop.
   cudaStream_t cs = nullptr, body_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
+  // Side stream of mto_run_host: host transfers that overlap the compute stream.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_aux = nullptr;
+  cudaEvent_t ev_chunk[mto::HOST_CHUNKS] = {};
   int nelx = 0, nely = 0;
   double nu = 0.3;
   unsigned fixed = 0;
@@ -73,8 +81,8 @@ struct mto_ctx {
   double* xdes = nullptr;
   size_t xdes_cap = 0;
   // host-call staging (mto_run_host)
-  double *hx = nullptr, *hf = nullptr, *hu = nullptr, *hc = nullptr, *hg = nullptr;
-  size_t hx_cap = 0, hf_cap = 0, hg_cap = 0;
+  double *hf = nullptr, *hu = nullptr, *hc = nullptr, *hg = nullptr;
+  size_t hf_cap = 0, hg_cap = 0;
   int hc_cap = 0;
   // graph of two PCG iterations (host-polled loop, used when kernel timing is on)
   cudaGraphExec_t gexec = nullptr;

@@ -130,9 +130,11 @@ struct PhaseTable {
 };
 // E_e = sum_i x_{e,i}^penal E_i (Eq. 5); ipenal >= 0 selects repeated products.
 // Also writes E (kA, kB, kC, kG) per element (Ek4, 4 doubles) for the float64 sweeps.
+// Element rows [j0, j1) (j1 < 0: to the last row).
 cudaError_t launch_modulus(const Grid& g, int n_phase, const double* x, PhaseTable ph, double penal,
                            int ipenal, double* E64, __nv_bfloat16* Ebf, double* Ek4,
-                           FineConst<double> kf, cudaStream_t s, int num_sms);
+                           FineConst<double> kf, cudaStream_t s, int num_sms, int j0 = 0,
+                           int j1 = -1);
 // w / D on the float64 finest level (D = KE_00 * sum of the four moduli).
 cudaError_t launch_fine_invd(const Grid& g, const double* E64, double w_over_kdiag, double* invd1,
                              cudaStream_t s, int num_sms);
@@ -163,9 +165,11 @@ cudaError_t prepare_cholesky_inverse(int n, int bw);
 // In-place band Cholesky of Kb (1 / L_ii to invL), then the explicit inverse.
 cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
                                     int* err_flag, cudaStream_t s, int num_sms);
-// dcdx (+)= -penal x^(penal-1) E_i w_e, w_e = u_e^T KE u_e (dense user layouts).
+// dcdx (+)= -penal x^(penal-1) E_i w_e, w_e = u_e^T KE u_e (dense user layouts),
+// on element rows [j0, j1) (j1 < 0: to the last row).
 cudaError_t launch_sensitivity(int nelx, int nely, int n_phase, const double* x, PhaseTable ph,
                                double penal, int ipenal, FineConst<double> kf, const double* u,
-                               double* dcdx, int accumulate, cudaStream_t s, int num_sms);
+                               double* dcdx, int accumulate, cudaStream_t s, int num_sms, int j0 = 0,
+                               int j1 = -1);
 
 }  // namespace mto

@@ -21,12 +21,14 @@ __device__ __forceinline__ double xpow(double x, double p, int ip) {
   return pow(x, p);
 }
 
-__global__ void modulus_kernel(Grid g, int n_phase, const double* __restrict__ x, PhaseTable ph,
-                               double penal, int ipenal, double* __restrict__ E64,
+// Element rows [j0, j1).
+__global__ void modulus_kernel(Grid g, int j0, int j1, int n_phase, const double* __restrict__ x,
+                               PhaseTable ph, double penal, int ipenal, double* __restrict__ E64,
                                __nv_bfloat16* __restrict__ Ebf, double* __restrict__ Ek4,
                                FineConst<double> kf) {
   const long long n = (long long)g.nx * g.ny;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+  const long long e1 = (long long)j1 * g.nx;
+  for (long long e = (long long)j0 * g.nx + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < e1;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e % g.nx), j = (int)(e / g.nx);
     double E = 0.0;
@@ -435,25 +437,30 @@ __global__ void __launch_bounds__(32)
   }
 }
 
-__global__ void sensitivity_kernel(int nelx, int nely, int n_phase, const double* __restrict__ x,
-                                   PhaseTable ph, double penal, int ipenal, FineConst<double> kf,
-                                   const double* __restrict__ u, double* __restrict__ dcdx,
-                                   int accumulate) {
+// Element rows [j0, j1).  cp[p] = -penal E_p, so that a phase costs three
+// FP64 operations (the kernel is bound by the FP64 pipe).
+__global__ void sensitivity_kernel(int nelx, int nely, int j0, int j1, int n_phase,
+                                   const double* __restrict__ x, PhaseTable cp, double penal,
+                                   int ipenal, FineConst<double> kf, const double* __restrict__ u,
+                                   double* __restrict__ dcdx, int accumulate) {
   const long long n = (long long)nelx * nely;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+  const long long e1 = (long long)j1 * nelx;
+  for (long long e = (long long)j0 * nelx + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < e1;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e % nelx), j = (int)(e / nelx);
     const long long n0 = (long long)j * (nelx + 1) + i, n3 = n0 + nelx + 1;
-    const double2 bl = make_double2(u[2 * n0], u[2 * n0 + 1]);
-    const double2 br = make_double2(u[2 * n0 + 2], u[2 * n0 + 3]);
-    const double2 tr = make_double2(u[2 * n3 + 2], u[2 * n3 + 3]);
-    const double2 tl = make_double2(u[2 * n3], u[2 * n3 + 1]);
+    const double2* u2 = reinterpret_cast<const double2*>(u);
+    const double2 bl = u2[n0], br = u2[n0 + 1], tr = u2[n3 + 1], tl = u2[n3];
     const Strain<double> w = strain_coords<double>(bl, br, tr, tl);
-    const Strain<double> t = fine_core<double>(w, 1.0, kf);
-    const double we = w.c1 * t.c1 + w.c3 * t.c3 + w.d2 * t.d2 + w.d3 * t.d3 + w.s * t.s;
+    // u_e^T KE u_e in the strain basis (E = 1): kA (c1^2 + d2^2) + 2 kB c1 d2
+    // + kC (c3^2 + d3^2) + kG s^2.
+    const double a = fma(kf.kA, w.c1, (2.0 * kf.kB) * w.d2);
+    const double b = fma(w.c3, w.c3, w.d3 * w.d3);
+    const double we = fma(w.c1, a, fma(kf.kA * w.d2, w.d2, fma(kf.kC, b, (kf.kG * w.s) * w.s)));
     for (int p = 0; p < n_phase; ++p) {
       const long long k = (long long)p * n + e;
-      const double g = -penal * xpow(x[k], penal - 1.0, ipenal >= 1 ? ipenal - 1 : -1) * ph.E[p] * we;
+      const double xp = xpow(x[k], penal - 1.0, ipenal >= 1 ? ipenal - 1 : -1);
+      const double g = (cp.E[p] * we) * xp;
       dcdx[k] = accumulate ? dcdx[k] + g : g;
     }
   }
@@ -470,9 +477,12 @@ static int blocks_for(long long n, int num_sms) {
 
 cudaError_t launch_modulus(const Grid& g, int n_phase, const double* x, PhaseTable ph, double penal,
                            int ipenal, double* E64, __nv_bfloat16* Ebf, double* Ek4,
-                           FineConst<double> kf, cudaStream_t s, int num_sms) {
-  modulus_kernel<<<blocks_for((long long)g.nx * g.ny, num_sms), 256, 0, s>>>(g, n_phase, x, ph, penal,
-                                                                             ipenal, E64, Ebf, Ek4, kf);
+                           FineConst<double> kf, cudaStream_t s, int num_sms, int j0, int j1) {
+  if (j1 < 0) j1 = g.ny;
+  if (j0 < 0 || j0 > j1 || j1 > g.ny) return cudaErrorInvalidValue;
+  if (j0 == j1) return cudaSuccess;
+  modulus_kernel<<<blocks_for((long long)g.nx * (j1 - j0), num_sms), 256, 0, s>>>(
+      g, j0, j1, n_phase, x, ph, penal, ipenal, E64, Ebf, Ek4, kf);
   return cudaGetLastError();
 }
 
@@ -701,9 +711,15 @@ cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, dou
 
 cudaError_t launch_sensitivity(int nelx, int nely, int n_phase, const double* x, PhaseTable ph,
                                double penal, int ipenal, FineConst<double> kf, const double* u,
-                               double* dcdx, int accumulate, cudaStream_t s, int num_sms) {
-  sensitivity_kernel<<<blocks_for((long long)nelx * nely, num_sms), 256, 0, s>>>(
-      nelx, nely, n_phase, x, ph, penal, ipenal, kf, u, dcdx, accumulate);
+                               double* dcdx, int accumulate, cudaStream_t s, int num_sms, int j0,
+                               int j1) {
+  if (j1 < 0) j1 = nely;
+  if (j0 < 0 || j0 > j1 || j1 > nely) return cudaErrorInvalidValue;
+  if (j0 == j1) return cudaSuccess;
+  PhaseTable cp{};
+  for (int p = 0; p < n_phase && p < 16; ++p) cp.E[p] = -penal * ph.E[p];
+  sensitivity_kernel<<<blocks_for((long long)nelx * (j1 - j0), num_sms), 256, 0, s>>>(
+      nelx, nely, j0, j1, n_phase, x, cp, penal, ipenal, kf, u, dcdx, accumulate);
   return cudaGetLastError();
 }
 
