@@ -168,9 +168,20 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   return MTO_OK;
 }
 
+// Whether the mixed-precision PCG step leaves r -= alpha q to the next
+// V-cycle's first smoothing sweep (FIN_PQ_FUSED / FIN_UPDATE_FUSED): that
+// sweep loads r anyway (as its float32 copy), and the update's FP64 work
+// overlaps the sweep's float32 work.
+bool fuse_update(const mto_ctx* c) { return c->mixed && c->o.nu1 >= 2; }
+
+// Residual of the PCG step of parity par (the buffers alternate only when
+// the update is fused).
+double2* rbuf(const mto_ctx* c, int par) { return (fuse_update(c) && par == 1) ? c->r_alt : c->r; }
+
 // V-cycle on the finest level with right-hand side r (float64).  With
-// with_dot, the last post-smoothing sweep also forms z.r (and z.q) and
-// finishes beta (FIN_RHO).
+// with_dot (inside the PCG loop), the last post-smoothing sweep also forms
+// z.r (and z.q) and finishes beta (FIN_RHO), and with fuse_update the first
+// sweep applies the pending CG update of r.
 template <typename T>
 mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx) {
   using T2 = typename V2<T>::t;
@@ -208,8 +219,15 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
     p.kf = fine_const<T>(c);
     p.invd1 = c->invd1;
     p.wdiag = T(c->w_over_kdiag);
-    if (dot) {
-      p.rdot = c->r;
+    if (dot && mode == MODE_SMOOTH0) {
+      // The CG update r -= alpha q of the last step (mixed precision).
+      p.r64 = rbuf(c, c->cur_par);
+      p.r64_prev = rbuf(c, c->cur_par ^ 1);
+      p.q64 = c->q;
+      p.out32 = c->r32;
+      p.finish = FIN_UPDATE_FUSED;
+    } else if (dot) {
+      p.rdot = rbuf(c, c->cur_par);
       p.qdot = c->o.flexible ? c->q : nullptr;
       p.finish = FIN_RHO;
     }
@@ -228,7 +246,7 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
   int first = 1;
   if (fused0) {
     CK(t0());
-    KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr, false));
+    KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr, fuse_update(c) && with_dot));
     CK(t1());
     first = 2;
   }
@@ -277,7 +295,7 @@ mto_status fine_resid(mto_ctx* c, const double2* v, const double2* b, double2* o
   p.finish = finish;
   p.xlag = xlag;
   p.xdir = xdir;
-  if (c->mixed && out == c->r) p.out32 = c->r32;
+  if (c->mixed && (out == c->r || out == c->r_alt)) p.out32 = c->r32;
   KL(launch_sweep<double>(SRC_FINE64, MODE_RESID, false, false, p,
                           target_warps64(c), c->num_sms, c->cs));
   return MTO_OK;
@@ -308,15 +326,16 @@ mto_status enqueue_iteration(mto_ctx* c, int par) {
     p.tag = par ^ 1;
     p.out = c->q;
     p.E = c->Ek4;
-    p.finish = FIN_PQ;
+    p.finish = fuse_update(c) ? FIN_PQ_FUSED : FIN_PQ;
     KL(launch_sweep<double>(SRC_FINE64, MODE_KP, false, c->mixed, p,
                             target_warps64(c), c->num_sms, c->cs));
   }
   if (c->timing) CK(cudaEventRecordWithFlags(c->kev[par][0][1], c->cs, cudaEventRecordExternal));
-  KL(launch_update(g, c->r, c->mixed ? c->r32 : nullptr, c->q, c->partials, c->ticket, c->sc,
-                   vec_blocks(g.size(), c->num_sms), c->cs));
+  if (!fuse_update(c))
+    KL(launch_update(g, c->r, c->mixed ? c->r32 : nullptr, c->q, c->partials, c->ticket, c->sc,
+                     vec_blocks(g.size(), c->num_sms), c->cs));
   if (c->mixed && c->o.rr_every > 0)
-    ST(fine_resid(c, c->x, c->f, c->r, FIN_REPLACE, 1, 1, 0, 1, c->p[par ^ 1]));
+    ST(fine_resid(c, c->x, c->f, rbuf(c, par ^ 1), FIN_REPLACE, 1, 1, 0, 1, c->p[par ^ 1]));
   return MTO_OK;
 }
 
@@ -809,6 +828,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   }
   ST(dalloc_t(c, &c->x, nf));
   ST(dalloc_t(c, &c->r, nf));
+  if (c->mixed) ST(dalloc_t(c, &c->r_alt, nf));
   ST(dalloc_t(c, &c->q, nf));
   ST(dalloc_t(c, &c->f, nf));
   ST(dalloc_t(c, &c->tmp, nf));

@@ -290,6 +290,9 @@ struct DevScalars {
   // bound by memory): x_lag = 1 while x is one step behind, p_par says which
   // search-direction buffer holds that p.
   int x_lag, p_par;
+  // Mixed precision: the update r -= alpha q of the last step is pending;
+  // the next V-cycle's first smoothing sweep applies it (FIN_UPDATE_FUSED).
+  int upd_pending;
 };
 
 // Outcome of one solve, copied from DevScalars at the end of each right-hand side.
@@ -308,7 +311,9 @@ enum Finish {
   FIN_PQ,         // sc->pq = s0; alpha
   FIN_UPDATE,     // sc->rr = s0; iter++; convergence
   FIN_REPLACE,    // sc->rr = s0 after residual replacement; convergence
-  FIN_TRUE        // sc->rr_true = s0
+  FIN_TRUE,       // sc->rr_true = s0
+  FIN_PQ_FUSED,   // as FIN_PQ, and the step is complete but for r -= alpha q
+  FIN_UPDATE_FUSED  // sc->rr = s0 after the fused r update, if one was pending
 };
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
@@ -355,7 +360,30 @@ __device__ __forceinline__ void finish_scalars(DevScalars* sc, int kind, double 
       else if (!replace_now && sc->iter >= sc->max_it) sc->done = MAXIT;
       break;
     }
+    case FIN_PQ_FUSED:
+      // K p has applied any pending x step; with alpha known the new x step
+      // and the r update are pending (applied by the next K p sweep and the
+      // next V-cycle's first sweep), so the iteration is counted here.
+      sc->x_lag = 0;
+      sc->p_par = tag;
+      sc->pq = s0;
+      if (!finite_pos(s0)) { sc->done = BREAKDOWN; break; }
+      sc->alpha = sc->rho / s0;
+      sc->x_lag = 1;
+      sc->upd_pending = 1;
+      sc->rho_prev = sc->rho;
+      sc->iter += 1;
+      break;
+    case FIN_UPDATE_FUSED:
+      if (!sc->upd_pending) break;  // the residual was replaced instead
+      sc->upd_pending = 0;
+      sc->rr = s0;
+      if (!(s0 < 1.0e300)) sc->done = BREAKDOWN;
+      else if (s0 <= sc->tol2 * sc->ff) sc->done = CONVERGED;
+      else if (sc->iter >= sc->max_it) sc->done = MAXIT;
+      break;
     case FIN_REPLACE:
+      sc->upd_pending = 0;
       sc->rr = s0;
       if (!(s0 < 1.0e300)) sc->done = BREAKDOWN;
       else if (s0 <= sc->tol2 * sc->ff) sc->done = CONVERGED;

@@ -59,6 +59,10 @@ struct mto_ctx {
   double2 *x = nullptr, *r = nullptr, *q = nullptr, *f = nullptr, *tmp = nullptr;
   double2* p[2] = {nullptr, nullptr};
   float2* r32 = nullptr;
+  // Mixed precision: the PCG step of parity par keeps r in (par ? r_alt : r).
+  // The first smoothing sweep applies the update r -= alpha q out of place,
+  // since neighbouring warps still read the old r on their halo rows.
+  double2* r_alt = nullptr;
   // coarsest grid
   int n0 = 0, bw0 = 0;
   int* dof_index = nullptr;

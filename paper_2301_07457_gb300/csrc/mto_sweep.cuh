@@ -95,6 +95,9 @@ template <typename T> struct SweepParams {
   T wdiag;              // float32 finest level: w / (KE_00 at E = 1); D = sum of 4 moduli
   const double2* rdot;  // dot partner for z.r
   const double2* qdot;  // dot partner for z.q (flexible beta), may be null
+  double2* r64;            // bf16 SMOOTH0 with the CG update: r of this step (written)
+  const double2* r64_prev;  // ... r of the last step, read while the update is pending
+  const double2* q64;       // ... and q = K p of the last step
   double* partials;
   unsigned* ticket;
   DevScalars* sc;

@@ -108,6 +108,7 @@ template <typename T, typename ZT> struct VRaw2 {
   T2 c00, c10, c01, c11;  // PSMOOTH: coarse nodes (I, Jlo), (I+1, Jlo), (I, Jhi), (I+1, Jhi)
   double2 d1;             // SMOOTH0, float64 finest level: w / D of the pair
   T2 d20, d21;            // SMOOTH0, coarse levels: w / D per DOF
+  double2 r0, r1, q0, q1;  // SMOOTH0 with the CG update: float64 r and q of the pair
 };
 
 // Node-row loads for the pair.
@@ -138,7 +139,8 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep2 {
   static constexpr bool E_AHEAD = SRC == SRC_FINEBF;
 
   // k: offset of node (i0, jj); i0 even.  lag (RESID): also load the
-  // direction of the pending x step.
+  // direction of the pending x step; (bf16 SMOOTH0 with the CG update): the
+  // update is pending, load the last step's r.
   __device__ __forceinline__ static void load_v(const SweepParams<T>& a, long long k, int i0, int jj,
                                                 VR& r, bool lag = false) {
     if constexpr (MODE == MODE_RESID) {
@@ -165,7 +167,12 @@ template <typename T, int SRC, int MODE, bool DOT, typename ZT> struct Sweep2 {
         r.c11 = r.c10;
       }
     } else if constexpr (MODE == MODE_SMOOTH0) {
-      ld_pair(a.b, k, r.v0, r.v1);
+      if constexpr (SRC == SRC_FINEBF && DOT) {  // the CG update forms b from r and q
+        ld_pair(lag ? a.r64_prev : static_cast<const double2*>(a.r64), k, r.r0, r.r1);
+        ld_pair(a.q64, k, r.q0, r.q1);
+      } else {
+        ld_pair(a.b, k, r.v0, r.v1);
+      }
       if constexpr (SRC == SRC_FINE64) r.d1 = reinterpret_cast<const double2*>(a.invd1)[k >> 1];
       else if constexpr (SRC != SRC_FINEBF) ld_pair(a.invd2, k, r.d20, r.d21);
     } else {
@@ -320,6 +327,18 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
   using NR = typename S2::NR;
   constexpr bool FBF = SRC == SRC_FINEBF;
   constexpr bool FBF0 = FBF && MODE == MODE_SMOOTH0;
+  // The bf16 pre-smoothing with DOT carries the CG update of the outer
+  // iteration (Alg. 2): r -= alpha q at every node row it loads, b = float(r)
+  // for the smoothing, and at the rows it owns the new r, its float32 copy
+  // and |r|^2 (into dot0).  Without a pending update (the first iteration,
+  // or one whose residual was just replaced) alpha is 0 and nothing is written.
+  constexpr bool UPD = FBF0 && DOT;
+  bool upd = false;
+  double aupd = 0.0;
+  if constexpr (UPD) {
+    upd = a.sc->upd_pending != 0;
+    aupd = upd ? a.sc->alpha : 0.0;
+  }
   const int strip = wg % a.nstrips;
   const int chunk = wg / a.nstrips;
   T beta = T(0);
@@ -340,6 +359,7 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
       alag = T(a.sc->alpha);
     }
   }
+  if constexpr (UPD) lag = upd;  // read the last step's r
 
   constexpr int STRIDE = MODE == MODE_RESTRICT ? SWEEP2_RSTRIDE : SWEEP2_STRIDE;
   const Grid g = a.g;
@@ -396,6 +416,28 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
       S2::load_n(a, ke, pk.n);
     };
 
+    // Right-hand side of a loaded node row (the float32 r of the V-cycle);
+    // with UPD, the CG update of that row, written back where `owned`.
+    auto take_b = [&](const VR& r, long long kk, bool owned, T2& b0, T2& b1) {
+      if constexpr (UPD) {
+        const double2 n0 = make_double2(fma(-aupd, r.q0.x, r.r0.x), fma(-aupd, r.q0.y, r.r0.y));
+        const double2 n1 = make_double2(fma(-aupd, r.q1.x, r.r1.x), fma(-aupd, r.q1.y, r.r1.y));
+        b0 = make_float2(d2f_rn(n0.x), d2f_rn(n0.y));
+        b1 = make_float2(d2f_rn(n1.x), d2f_rn(n1.y));
+        if (upd && owned) {  // uniform over the warp
+          st_pair(a.r64, kk, n0, n1, own0, own1);
+          st_pair(a.out32, kk, b0, b1, own0, own1);
+          if (own0) dot0 = fma(n0.x, n0.x, fma(n0.y, n0.y, dot0));
+          if (own1) dot0 = fma(n1.x, n1.x, fma(n1.y, n1.y, dot0));
+        }
+      } else {
+        (void)kk;
+        (void)owned;
+        b0 = r.v0;
+        b1 = r.v1;
+      }
+    };
+
     const long long k0 = g.at(i0, je0);
     // bf16 moduli of the current element row (and of the row below for D);
     // ecl, epl: element i0 - 1 (SMOOTH0).
@@ -423,6 +465,8 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
     {
       VR r0;
       S2::load_v(a, k0, i0, je0, r0, lag);
+      T2 b0r = mk2<T>(T(0), T(0)), b1r = b0r;
+      if constexpr (MODE == MODE_SMOOTH0) take_b(r0, k0, false, b0r, b1r);  // row of the chunk below
       if constexpr (FBF0) {
         float w0, w1;
         fbf_winv_own(epl, ep0, ep1, ecl, ec0, ec1, float(a.wdiag), w0, w1);
@@ -432,14 +476,14 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
         const bool a1 = rowok && i0 + 1 >= 0 && i0 + 1 <= g.nx && !cfix1;
         wc0 = a0 ? mk2<T>(w0, w0) : mk2<T>(T(0), T(0));
         wc1 = a1 ? mk2<T>(w1, w1) : mk2<T>(T(0), T(0));
-        vb0 = mk2<T>(wc0.x * r0.v0.x, wc0.y * r0.v0.y);
-        vb1 = mk2<T>(wc1.x * r0.v1.x, wc1.y * r0.v1.y);
+        vb0 = mk2<T>(wc0.x * b0r.x, wc0.y * b0r.y);
+        vb1 = mk2<T>(wc1.x * b1r.x, wc1.y * b1r.y);
       } else {
         S2::finish_v(a, r0, i0, je0, beta, vb0, vb1, lag, alag);
       }
       if constexpr (MODE == MODE_SMOOTH0) {
-        bc0 = r0.v0;
-        bc1 = r0.v1;
+        bc0 = b0r;
+        bc1 = b1r;
         if constexpr (SRC == SRC_FINE64) {
           wc0 = mk2<T>(T(r0.d1.x), T(r0.d1.x));
           wc1 = mk2<T>(T(r0.d1.y), T(r0.d1.y));
@@ -486,7 +530,7 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
           }
         }
         DRaw2 dcur;
-        if constexpr (DOT) {
+        if constexpr (DOT && !UPD) {
           if (je > je0) S2::load_d(a, k, dcur);
         }
 
@@ -494,6 +538,8 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
         T2 vt0, vt1;
         float en0 = 0.f, en1 = 0.f, enl = 0.f;  // bf16 moduli of element row je + 1
         T2 wt0 = zero2, wt1 = zero2;
+        T2 btop0 = zero2, btop1 = zero2;  // SMOOTH0: right-hand side of row je + 1
+        if constexpr (MODE == MODE_SMOOTH0) take_b(cur.vt, k + pitch, je + 1 <= je1, btop0, btop1);
         if constexpr (FBF) {
           en0 = bf_lo(cur.e.E);
           en1 = bf_hi(cur.e.E);
@@ -509,8 +555,8 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
           const bool a1 = rowok && i0 + 1 >= 0 && i0 + 1 <= g.nx && !cfix1;
           wt0 = a0 ? mk2<T>(w0, w0) : zero2;
           wt1 = a1 ? mk2<T>(w1, w1) : zero2;
-          vt0 = mk2<T>(wt0.x * cur.vt.v0.x, wt0.y * cur.vt.v0.y);
-          vt1 = mk2<T>(wt1.x * cur.vt.v1.x, wt1.y * cur.vt.v1.y);
+          vt0 = mul2(wt0, btop0);
+          vt1 = mul2(wt1, btop1);
         } else {
           S2::finish_v(a, cur.vt, i0, je + 1, beta, vt0, vt1, lag, alag);
         }
@@ -616,7 +662,7 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
           const T2 z0 = fma2(d0, sub2(b0, kv0), vb0);
           const T2 z1 = fma2(d1, sub2(b1, kv1), vb1);
           st_pair(a.out, k, z0, z1, inb0, inb1);
-          if constexpr (DOT) {
+          if constexpr (DOT && !UPD) {
             // Inactive nodes contribute 0 (z and r vanish there).
             if (inb0) {
               const double zx = to_f64(z0.x), zy = to_f64(z0.y);
@@ -653,8 +699,8 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
           }
         }
         if constexpr (MODE == MODE_SMOOTH0) {
-          bc0 = cur.vt.v0;
-          bc1 = cur.vt.v1;
+          bc0 = btop0;
+          bc1 = btop1;
           if constexpr (FBF0) {
             wc0 = wt0;
             wc1 = wt1;

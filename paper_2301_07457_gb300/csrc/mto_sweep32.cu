@@ -11,6 +11,7 @@ namespace mto {
 // loads takes.
 template <int SRC, int MODE, bool DOT> constexpr int lookahead() {
   if (SRC == SRC_CMOM && MODE == MODE_PSMOOTH) return 1;
+  if (SRC == SRC_FINEBF && MODE == MODE_SMOOTH0 && DOT) return 1;  // float64 r and q per row
   if (DOT || MODE == MODE_PSMOOTH || SRC == SRC_CFINE || SRC == SRC_CMOM) return 2;
   return 3;
 }
@@ -43,7 +44,9 @@ cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepP
       case MODE_SMOOTH:
         return dot ? go<SRC_FINEBF, MODE_SMOOTH, true>(p, tw, num_sms, s)
                    : go<SRC_FINEBF, MODE_SMOOTH, false>(p, tw, num_sms, s);
-      case MODE_SMOOTH0: return go<SRC_FINEBF, MODE_SMOOTH0, false>(p, tw, num_sms, s);
+      case MODE_SMOOTH0:  // with dot: carrying the CG update
+        return dot ? go<SRC_FINEBF, MODE_SMOOTH0, true>(p, tw, num_sms, s)
+                   : go<SRC_FINEBF, MODE_SMOOTH0, false>(p, tw, num_sms, s);
       case MODE_PSMOOTH:
         return dot ? go<SRC_FINEBF, MODE_PSMOOTH, true>(p, tw, num_sms, s)
                    : go<SRC_FINEBF, MODE_PSMOOTH, false>(p, tw, num_sms, s);
