@@ -32,16 +32,18 @@ SEED = 0
 #    operations (11 edge-difference add/sub, 7 core mul/fma on pre-scaled
 #    moduli, 14 edge-force add/sub, 2 fma for p, 2 fma for the dot);
 #  * float32 fused pre-smoothing (two damped-Jacobi sweeps from zero, the
-#    first formed on the fly): reads b (8 B) and the element's bf16 modulus
-#    (2 B), writes z (8 B): 18 B.
+#    first formed on the fly) carrying the CG update r -= alpha q of the last
+#    step: reads the last r and q (float64, 16 B each) and the element's bf16
+#    modulus (2 B), writes the new r (16 B), its float32 copy (8 B) and z
+#    (8 B): 66 B.
 KP_OPS_PER_NODE = 36
-SMOOTH32_BYTES_PER_NODE = 18
+SMOOTH32_BYTES_PER_NODE = 66
 SMOOTH64_OPS_PER_NODE = 38  # K v 32, w D^-1 b 2, z + d (b - K v) 4 (first two sweeps fused)
 # DRAM bytes per launch at 2048^2 from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/sweeps_2048_ncu_full.md); None once the
 # kernel changes.
-KP_TRAFFIC = 354_637_568
-SMOOTH32_TRAFFIC = 45_084_928
+KP_TRAFFIC = 354_025_984
+SMOOTH32_TRAFFIC = 248_203_264
 # FP64 pipe: 2 operations per clock per SM (1.25 TFLOP/s nominal at 2 flops
 # per FMA), 152 SMs, 2070 MHz.
 FP64_OPS_PEAK = 2 * 152 * 2.070e9
@@ -430,7 +432,8 @@ def run_ours(args):
                 "frac": kp_ops / FP64_OPS_PEAK, "traffic": KP_TRAFFIC, "ms_per_launch": kp_ms,
                 "samples": kt["samples"][0],
                 "peak_kind": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
-    roofline_vcycle = {"bound": "hbm", "kernel": "finest fused pre-smoothing (float32, bf16 E)",
+    roofline_vcycle = {"bound": "hbm",
+                       "kernel": "finest fused pre-smoothing with the CG update (float32, bf16 E; float64 r)",
                        "achieved": sm_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
                        "frac": sm_bytes / 1e9 / hbm_peak, "traffic": SMOOTH32_TRAFFIC,
                        "ms_per_launch": sm_ms, "samples": kt["samples"][1], "peak_kind": peak_kind}

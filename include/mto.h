@@ -179,7 +179,10 @@ mto_status mto_compliance_grad(mto_ctx* ctx, int n_rhs, const double* f_dev, con
  * compliances and the sensitivities back.  x_host [n_phase][nely][nelx],
  * f_host/u_host [n_rhs][nely+1][nelx+1][2], compliance_host [n_rhs],
  * dcdx_host [n_phase][nely][nelx] (may be NULL).  Host arrays may be
- * pageable or pinned; the call synchronises. */
+ * pageable or pinned (pinned ones let the transfers overlap the kernels: x
+ * arrives in row chunks whose moduli are formed while the next chunk is in
+ * flight, f during set-up, u and dcdx while the sensitivities are formed);
+ * the call synchronises.  stats->ms_setup includes the transfer of x. */
 mto_status mto_run_host(mto_ctx* ctx, int n_phase, const double* x_host, const double* E_phase,
                         double penal, int n_rhs, const double* f_host, double* u_host,
                         double* compliance_host, double* dcdx_host, mto_solve_stats* stats);
