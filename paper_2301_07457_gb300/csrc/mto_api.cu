@@ -562,8 +562,8 @@ mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, cons
 
 mto_status enqueue_hierarchy(mto_ctx* c) {
   const Grid& gf = c->lv[c->L].g;
-  if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->cs, c->num_sms));
   const int redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
+  // Moments down the hierarchy (each level from the one above).
   for (int l = c->L - 1; l >= 0; --l) {
     LevelBuf& B = c->lv[l];
     if (l == c->L - 1) {
@@ -573,28 +573,38 @@ mto_status enqueue_hierarchy(mto_ctx* c) {
       KL(launch_moments_from_coarse(B.g, c->lv[l + 1].g, c->lv[l + 1].mom, redisc, B.mom, c->cs,
                                     c->num_sms));
     }
-    if (c->mixed) {
-      // Level L-1 rebuilds its elements from the bf16 fine moduli; deeper
-      // levels read scaled moments; level 0 is solved directly.
-      if (l > 0 && l < c->L - 1) KL(launch_kmom(B.g, B.mom, c->nu, (float*)B.coef, c->cs, c->num_sms));
-      if (l > 0)
-        KL(launch_coarse_invd<float>(B.g, B.mom, c->nu, c->o.omega, (float2*)B.invd2, c->cs,
-                                     c->num_sms));
-    } else {
-      KL(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->cs, c->num_sms));
-      if (l > 0)
-        KL(launch_coarse_invd<double>(B.g, B.mom, c->nu, c->o.omega, (double2*)B.invd2, c->cs,
-                                      c->num_sms));
-    }
   }
+  // The coarsest factor and inverse (one SM for the factor, a serial chain)
+  // run on a side stream while this one prepares the smoothers and the
+  // element data of the other levels, which they do not depend on.
   LevelBuf& B0 = c->lv[0];
   KL(launch_coefs<double>(B0.g, B0.mom, c->nu, B0.coef64, c->cs, c->num_sms));
   CK(cudaMemsetAsync(c->Kd, 0, sizeof(double) * c->n0 * (c->bw0 + 1), c->cs));
   CK(cudaMemsetAsync(c->err_flag, 0, sizeof(int), c->cs));
   KL(launch_band_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->bw0, c->Kd, c->cs));
-  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Kinv, c->err_flag, c->cs,
+  CK(cudaEventRecord(c->ev_fork, c->cs));
+  CK(cudaStreamWaitEvent(c->fac_stream, c->ev_fork, 0));
+  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Kinv, c->err_flag, c->fac_stream,
                              c->num_sms));
   c->launches += 1;  // the inverse is a second kernel
+  CK(cudaEventRecord(c->ev_join, c->fac_stream));
+  if (!c->mixed) KL(launch_fine_invd(gf, c->E64, c->w_over_kdiag, c->invd1, c->cs, c->num_sms));
+  for (int l = c->L - 1; l >= 1; --l) {
+    LevelBuf& B = c->lv[l];
+    if (c->mixed) {
+      // Level L-1 rebuilds its elements from the bf16 fine moduli; deeper
+      // levels read scaled moments; level 0 is solved directly.
+      if (l < c->L - 1) KL(launch_kmom(B.g, B.mom, c->nu, (float*)B.coef, c->cs, c->num_sms));
+      KL(launch_coarse_invd<float>(B.g, B.mom, c->nu, c->o.omega, (float2*)B.invd2, c->cs, c->num_sms));
+    } else {
+      KL(launch_coefs<double>(B.g, B.mom, c->nu, (double*)B.coef, c->cs, c->num_sms));
+      KL(launch_coarse_invd<double>(B.g, B.mom, c->nu, c->o.omega, (double2*)B.invd2, c->cs,
+                                    c->num_sms));
+    }
+  }
+  if (!c->mixed)  // the float64 level-0 coefficients of the sweeps (apply_operator)
+    KL(launch_coefs<double>(B0.g, B0.mom, c->nu, (double*)B0.coef, c->cs, c->num_sms));
+  CK(cudaStreamWaitEvent(c->cs, c->ev_join, 0));
   return MTO_OK;
 }
 
@@ -756,6 +766,9 @@ void mto_destroy(mto_ctx* c) {
   for (cudaEvent_t e : c->ev_chunk)
     if (e) cudaEventDestroy(e);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->fac_stream) cudaStreamDestroy(c->fac_stream);
   if (c->body_stream) cudaStreamDestroy(c->body_stream);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -782,6 +795,9 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   CK(cudaEventCreate(&c->ev_a));
   CK(cudaEventCreate(&c->ev_b));
   CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->fac_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming));
   for (cudaEvent_t& e : c->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CK(cudaMallocHost(&c->sc_host, sizeof(DevScalars)));

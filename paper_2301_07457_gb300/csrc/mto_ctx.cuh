@@ -40,6 +40,10 @@ struct mto_ctx {
   // captures the body of the solver's device-side loop.
   cudaStream_t cs = nullptr, body_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
+  // Side stream of set_design: the coarsest factor and inverse, joined back
+  // before the call's work ends.
+  cudaStream_t fac_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Side stream of mto_run_host: host transfers that overlap the compute stream.
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_aux = nullptr;

@@ -138,13 +138,20 @@ __global__ void __launch_bounds__(VEC_NT)
     dot_kernel(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
                double* partials, unsigned* ticket, DevScalars* sc, int finish, double* out_value) {
   pdl_wait();
-  double acc = 0.0;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const double2 x = a[k], y = b[k];
-    acc = fma(x.x, y.x, fma(x.y, y.y, acc));
+  // Two nodes per pass into two FMA chains, the loads issued first.
+  double acc0 = 0.0, acc1 = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + stride < n; k += 2 * stride) {
+    const double2 x0 = a[k], y0 = b[k], x1 = a[k + stride], y1 = b[k + stride];
+    acc0 = fma(x0.x, y0.x, fma(x0.y, y0.y, acc0));
+    acc1 = fma(x1.x, y1.x, fma(x1.y, y1.y, acc1));
   }
-  block_reduce_finish<VEC_NT>(acc, 0.0, partials, ticket, sc, finish, out_value);
+  if (k < n) {
+    const double2 x = a[k], y = b[k];
+    acc0 = fma(x.x, y.x, fma(x.y, y.y, acc0));
+  }
+  block_reduce_finish<VEC_NT>(acc0 + acc1, 0.0, partials, ticket, sc, finish, out_value);
 }
 
 __global__ void pack_kernel(Grid g, const double* __restrict__ src, double2* __restrict__ dst,
