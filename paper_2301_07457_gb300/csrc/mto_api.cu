@@ -158,9 +158,17 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   } else {
     ST(coarse_cycle<T>(c, l - 1, sc, &cidx));
   }
-  KL(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));
+  // Post-smoothing; on the float32 levels the prolongation sweep and the
+  // next one run fused (mto_post2.cuh).
+  int s = 1;
+  if ((src == SRC_CMOM || src == SRC_CFINE) && c->o.nu2 >= 2) {
+    KL(sweep(MODE_POST2, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));
+    s = 2;
+  } else {
+    KL(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));
+  }
   cur ^= 1;
-  for (int s = 1; s < c->o.nu2; ++s) {
+  for (; s < c->o.nu2; ++s) {
     KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
     cur ^= 1;
   }

@@ -4,6 +4,7 @@
 
 #include <utility>
 
+#include "mto_post2.cuh"
 #include "mto_sweep2.cuh"
 
 namespace mto {

@@ -60,7 +60,8 @@ enum Mode {
   MODE_SMOOTH,
   MODE_PSMOOTH,
   MODE_RESTRICT,
-  MODE_SMOOTH0
+  MODE_SMOOTH0,
+  MODE_POST2  // float32 coarse levels: prolongation + two sweeps, fused (mto_post2.cuh)
 };
 
 template <typename T> struct SweepParams {

@@ -21,7 +21,8 @@ static cudaError_t go(SweepParams<float> p, int tw, int num_sms, cudaStream_t s)
   constexpr int COLS = sweep_cols_of(false, SRC, MODE);
   constexpr int PF = lookahead<SRC, MODE, DOT>();
   void (*kernel)(SweepParams<float>);
-  if constexpr (COLS == 2) kernel = sweep2_kernel<float, SRC, MODE, DOT, float2, PF>;
+  if constexpr (MODE == MODE_POST2) kernel = post2_kernel<SRC, 2>;
+  else if constexpr (COLS == 2) kernel = sweep2_kernel<float, SRC, MODE, DOT, float2, PF>;
   else kernel = sweep_kernel<float, SRC, MODE, DOT, float2, PF>;
   if (tw <= 0) {
     static const int wave = full_wave_warps(kernel, num_sms);  // same for every device of a run
@@ -61,6 +62,7 @@ cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepP
       case MODE_SMOOTH0: return go<SRC_CFINE, MODE_SMOOTH0, false>(p, tw, num_sms, s);
       case MODE_PSMOOTH: return go<SRC_CFINE, MODE_PSMOOTH, false>(p, tw, num_sms, s);
       case MODE_RESTRICT: return go<SRC_CFINE, MODE_RESTRICT, false>(p, tw, num_sms, s);
+      case MODE_POST2: return go<SRC_CFINE, MODE_POST2, false>(p, tw, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -71,6 +73,7 @@ cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepP
       case MODE_SMOOTH0: return go<SRC_CMOM, MODE_SMOOTH0, false>(p, tw, num_sms, s);
       case MODE_PSMOOTH: return go<SRC_CMOM, MODE_PSMOOTH, false>(p, tw, num_sms, s);
       case MODE_RESTRICT: return go<SRC_CMOM, MODE_RESTRICT, false>(p, tw, num_sms, s);
+      case MODE_POST2: return go<SRC_CMOM, MODE_POST2, false>(p, tw, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -8,7 +8,15 @@ namespace mto {
 
 SweepShape sweep_shape(const Grid& g, int mode, int target_warps, int cols) {
   SweepShape sh;
-  if (mode == MODE_RESTRICT) {
+  if (mode == MODE_POST2) {
+    // 60 output columns per warp, rows as for a smoothing sweep.
+    sh.nstrips = (g.nx + 1 + POST2_STRIDE - 1) / POST2_STRIDE;
+    const int want = target_warps / sh.nstrips > 1 ? target_warps / sh.nstrips : 1;
+    int h = (g.ny + 1 + want - 1) / want;
+    h = h < 1 ? 1 : (h > 64 ? 64 : h);
+    sh.H = h;
+    sh.nchunks = (g.ny + 1 + h - 1) / h;
+  } else if (mode == MODE_RESTRICT) {
     // Coarse columns per warp: 14 (one column per lane) or 30 (two).
     const int cstride = cols == 2 ? SWEEP2_RSTRIDE / 2 : SWEEP_RSTRIDE / 2;
     const int nxc = g.nx / 2, nyc = g.ny / 2;
