@@ -139,18 +139,25 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     return launch_sweep<T>(src, mode, false, false, p, tw, c->num_sms, c->cs);
   };
   // Pre-smoothing from U = 0: the first sweep (U = w D^-1 F) is formed on the
-  // fly inside the second when there are two or more.
-  if (c->o.nu1 >= 2) {
-    KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr));
+  // fly inside the second when there are two or more.  With exactly two on a
+  // float32 level, the residual and its restriction run in the same pass
+  // (mto_fused.cuh).
+  const bool fused_pre = (src == SRC_CMOM || src == SRC_CFINE) && c->o.nu1 == 2;
+  if (fused_pre) {
+    KL(sweep(MODE_PRE2, nullptr, (T2*)L.z[0], nullptr));
   } else {
-    KL(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb,
-                                c->cs));
+    if (c->o.nu1 >= 2) {
+      KL(sweep(MODE_SMOOTH0, nullptr, (T2*)L.z[0], nullptr));
+    } else {
+      KL(launch_jacobi0_coarse<T>(L.g, (const T2*)L.invd2, (const T2*)L.b, (T2*)L.z[0], sc, nb,
+                                  c->cs));
+    }
+    for (int s = 2; s < c->o.nu1; ++s) {
+      KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
+      cur ^= 1;
+    }
+    KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
   }
-  for (int s = 2; s < c->o.nu1; ++s) {
-    KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
-    cur ^= 1;
-  }
-  KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
   int cidx = 0;
   if (l - 1 == 0) {
     KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
@@ -159,7 +166,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     ST(coarse_cycle<T>(c, l - 1, sc, &cidx));
   }
   // Post-smoothing; on the float32 levels the prolongation sweep and the
-  // next one run fused (mto_post2.cuh).
+  // next one run fused (mto_fused.cuh).
   int s = 1;
   if ((src == SRC_CMOM || src == SRC_CFINE) && c->o.nu2 >= 2) {
     KL(sweep(MODE_POST2, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx]));

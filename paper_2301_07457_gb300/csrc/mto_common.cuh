@@ -54,7 +54,9 @@ inline Grid make_grid(int nx, int ny, unsigned fixed) {
   // Lanes of the marching sweeps read up to column nx + 62 (two columns per
   // lane) and down to column -2.
   g.pitch = ((OFFX + nx + 66) + 31) / 32 * 32;
-  g.rows = ny + 4;
+  // Rows -1 .. ny + 3: the fused pre-smoothing and restriction marches two
+  // rows past the last node row.
+  g.rows = ny + 5;
   g.fixed = fixed;
   return g;
 }

@@ -4,7 +4,7 @@
 
 #include <utility>
 
-#include "mto_post2.cuh"
+#include "mto_fused.cuh"
 #include "mto_sweep2.cuh"
 
 namespace mto {

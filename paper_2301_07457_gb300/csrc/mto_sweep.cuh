@@ -61,7 +61,8 @@ enum Mode {
   MODE_PSMOOTH,
   MODE_RESTRICT,
   MODE_SMOOTH0,
-  MODE_POST2  // float32 coarse levels: prolongation + two sweeps, fused (mto_post2.cuh)
+  MODE_POST2,  // float32 coarse levels: prolongation + two sweeps, fused (mto_fused.cuh)
+  MODE_PRE2    // float32 coarse levels: two sweeps from zero + residual + restriction, fused
 };
 
 template <typename T> struct SweepParams {

@@ -22,6 +22,7 @@ static cudaError_t go(SweepParams<float> p, int tw, int num_sms, cudaStream_t s)
   constexpr int PF = lookahead<SRC, MODE, DOT>();
   void (*kernel)(SweepParams<float>);
   if constexpr (MODE == MODE_POST2) kernel = post2_kernel<SRC, 2>;
+  else if constexpr (MODE == MODE_PRE2) kernel = pre2_kernel<SRC, 2>;
   else if constexpr (COLS == 2) kernel = sweep2_kernel<float, SRC, MODE, DOT, float2, PF>;
   else kernel = sweep_kernel<float, SRC, MODE, DOT, float2, PF>;
   if (tw <= 0) {
@@ -63,6 +64,7 @@ cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepP
       case MODE_PSMOOTH: return go<SRC_CFINE, MODE_PSMOOTH, false>(p, tw, num_sms, s);
       case MODE_RESTRICT: return go<SRC_CFINE, MODE_RESTRICT, false>(p, tw, num_sms, s);
       case MODE_POST2: return go<SRC_CFINE, MODE_POST2, false>(p, tw, num_sms, s);
+      case MODE_PRE2: return go<SRC_CFINE, MODE_PRE2, false>(p, tw, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -74,6 +76,7 @@ cudaError_t launch_sweep<float>(int src, int mode, bool dot, bool zfloat, SweepP
       case MODE_PSMOOTH: return go<SRC_CMOM, MODE_PSMOOTH, false>(p, tw, num_sms, s);
       case MODE_RESTRICT: return go<SRC_CMOM, MODE_RESTRICT, false>(p, tw, num_sms, s);
       case MODE_POST2: return go<SRC_CMOM, MODE_POST2, false>(p, tw, num_sms, s);
+      case MODE_PRE2: return go<SRC_CMOM, MODE_PRE2, false>(p, tw, num_sms, s);
       default: return cudaErrorInvalidValue;
     }
   }

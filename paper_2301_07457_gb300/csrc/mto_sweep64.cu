@@ -8,7 +8,17 @@ namespace mto {
 
 SweepShape sweep_shape(const Grid& g, int mode, int target_warps, int cols) {
   SweepShape sh;
-  if (mode == MODE_POST2) {
+  if (mode == MODE_PRE2) {
+    // 29 output coarse columns per warp, coarse rows per task as for the
+    // restriction sweep.
+    const int nxc = g.nx / 2, nyc = g.ny / 2;
+    sh.nstrips = (nxc + 1 + PRE2_CSTRIDE - 1) / PRE2_CSTRIDE;
+    const int want = target_warps / sh.nstrips > 1 ? target_warps / sh.nstrips : 1;
+    int hc = (nyc + 1 + want - 1) / want;
+    hc = hc < 1 ? 1 : (hc > 32 ? 32 : hc);
+    sh.H = 2 * hc;
+    sh.nchunks = (nyc + 1 + hc - 1) / hc;
+  } else if (mode == MODE_POST2) {
     // 60 output columns per warp, rows as for a smoothing sweep.
     sh.nstrips = (g.nx + 1 + POST2_STRIDE - 1) / POST2_STRIDE;
     const int want = target_warps / sh.nstrips > 1 ? target_warps / sh.nstrips : 1;
