@@ -52,6 +52,11 @@ __device__ __forceinline__ void st_pair(double2* p, long long k, double2 a, doub
   if (w1) p[k + 1] = b;
 }
 
+// L2 prefetch hint for the 32 bytes of a pair (no registers, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Element data of the pair (i0, j), (i1, j).
 template <typename T, int SRC> struct ERaw2;
 template <typename T> struct ERaw2<T, SRC_FINE64> {
@@ -532,6 +537,18 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
         DRaw2 dcur;
         if constexpr (DOT && !UPD) {
           if (je > je0) S2::load_d(a, k, dcur);
+          // The float64 operands two rows up go to L2 now, so that their loads
+          // there find them on chip.
+          if (je + 2 <= je1) {
+            prefetch_l2(a.rdot + k + 2 * pitch);
+            if (a.qdot != nullptr) prefetch_l2(a.qdot + k + 2 * pitch);
+          }
+        }
+        if constexpr (UPD) {
+          if (je + PF + 2 <= je1) {  // the last step's r and q, rows beyond the ring
+            prefetch_l2((lag ? a.r64_prev : a.r64) + k + (PF + 2) * pitch);
+            prefetch_l2(a.q64 + k + (PF + 2) * pitch);
+          }
         }
 
         // ---- top row je + 1 ----
