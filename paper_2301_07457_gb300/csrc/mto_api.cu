@@ -599,7 +599,7 @@ mto_status enqueue_hierarchy(mto_ctx* c) {
   KL(launch_band_assemble(B0.g, B0.coef64, c->dof_index, c->n0, c->bw0, c->Kd, c->cs));
   CK(cudaEventRecord(c->ev_fork, c->cs));
   CK(cudaStreamWaitEvent(c->fac_stream, c->ev_fork, 0));
-  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Kinv, c->err_flag, c->fac_stream,
+  KL(launch_cholesky_inverse(c->n0, c->bw0, c->Kd, c->invL, c->Lsc, c->Kinv, c->err_flag, c->fac_stream,
                              c->num_sms));
   c->launches += 1;  // the inverse is a second kernel
   CK(cudaEventRecord(c->ev_join, c->fac_stream));
@@ -903,6 +903,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   CK(cudaMemcpy(c->dof_index, dof.data(), sizeof(int) * dof.size(), cudaMemcpyHostToDevice));
   ST(dalloc_t(c, &c->Kd, (size_t)c->n0 * (c->bw0 + 1)));
   ST(dalloc_t(c, &c->invL, (size_t)c->n0));
+  ST(dalloc_t(c, &c->Lsc, 2 * (size_t)c->n0 * (c->bw0 + 1)));
   ST(dalloc_t(c, &c->Kinv, (size_t)c->n0 * c->n0));
   ST(dalloc_t(c, &c->err_flag, 1));
 

@@ -71,6 +71,7 @@ struct mto_ctx {
   int n0 = 0, bw0 = 0;
   int* dof_index = nullptr;
   double *Kd = nullptr, *Kinv = nullptr, *invL = nullptr;  // Kd: band storage of K_0 / its factor
+  double* Lsc = nullptr;  // the factor scaled by its columns' and rows' pivots (inverse)
   int* err_flag = nullptr;
   // reductions
   double* partials = nullptr;

@@ -163,8 +163,10 @@ cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int*
 // Opt-in shared memory of the coarsest factorisation kernels (once per size,
 // outside any stream capture).
 cudaError_t prepare_cholesky_inverse(int n, int bw);
-// In-place band Cholesky of Kb (1 / L_ii to invL), then the explicit inverse.
-cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
+// In-place band Cholesky of Kb (1 / L_ii to invL; the factor scaled by its
+// columns' and rows' pivots to Lsc, 2 n (bw + 1) doubles), then the explicit
+// inverse.
+cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Lsc, double* Kinv,
                                     int* err_flag, cudaStream_t s, int num_sms);
 // dcdx (+)= -penal x^(penal-1) E_i w_e, w_e = u_e^T KE u_e (dense user layouts),
 // on element rows [j0, j1) (j1 < 0: to the last row).

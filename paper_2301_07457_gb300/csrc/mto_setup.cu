@@ -297,7 +297,7 @@ constexpr int CHOL_NT = 512;
 
 template <bool SMEM>
 __global__ void __launch_bounds__(CHOL_NT)
-    cholesky_band_kernel(int n, int bw, double* Bg, double* invL, int* err) {
+    cholesky_band_kernel(int n, int bw, double* Bg, double* invL, double* Lsc, int* err) {
   extern __shared__ double dyn[];
   __shared__ double piv_s;
   const int W = bw + 1;
@@ -349,6 +349,14 @@ __global__ void __launch_bounds__(CHOL_NT)
   }
   if (SMEM)
     for (int t = tid; t < n * W; t += CHOL_NT) Bg[t] = B[t];
+  // The factor scaled by the pivots of its columns (Lsc[0 .. nW)) and of its
+  // rows (Lsc[nW .. 2nW)), for the two substitutions of the inverse.
+  for (int t = tid; t < n * W; t += CHOL_NT) {
+    const int r = t / W, c = r - (t - r * W);
+    const double v = B[t];
+    Lsc[t] = c >= 0 ? v * invL[c] : 0.0;
+    Lsc[(size_t)n * W + t] = v * invL[r];
+  }
 }
 
 // K_0^-1 by columns: L y = e_j (forward), then L^T x = y (backward), column j
@@ -551,33 +559,39 @@ static int max_dyn_smem() {
 // K_0^-1 by columns with column-oriented (axpy) substitution: one warp per
 // column j, four columns per block.  Forward, L y = e_j: at row k the warp
 // has the running sum acc_k = sum_{m<k} L_km y_m ready, forms
-// y_k = (delta_kj - acc_k) / L_kk (every lane the same value), and adds
-// L_rk y_k to the sums of the next bw rows r.  The sums of a window of
-// 32 NS rows live in registers: row r in lane r mod 32, slot (r / 32) mod NS,
-// so a row's sum is broadcast by one shuffle and each step costs one FP64
-// operation per slot and lane (no reduction).  Backward, L^T x = y, runs the
-// same way from the last row up.  Column j of K_0^-1 is row j (symmetric).
-// With LSMEM the band factor is staged in shared memory for the block; each
-// warp keeps its y in shared memory between the two passes.
+// yh_k = delta_kj - acc_k = y_k L_kk (every lane the same value), and adds
+// (L_rk / L_kk) yh_k to the sums of the next bw rows r, so the dependent chain
+// of a step is one shuffle and one FP64 operation; y = yh / L_kk is formed in
+// bulk after the pass.  The sums of a window of 32 NS rows live in
+// registers: row r in lane r mod 32, slot (r / 32) mod NS, so a row's sum is
+// broadcast by one shuffle and each step costs one FP64 operation per slot
+// and lane (no reduction).  Backward, L^T x = y, runs the same way from the
+// last row up with the factor scaled by its rows' pivots.  Column j of
+// K_0^-1 is row j (symmetric).  Lsc holds the factor scaled by the pivots of
+// its columns, then of its rows (cholesky_band_kernel); with LSMEM the block
+// stages each in shared memory for its pass; each warp keeps its y in shared
+// memory between the two passes.
 constexpr int INVA_WARPS = 4;
 
 template <bool LSMEM, int NS>
 __global__ void __launch_bounds__(32 * INVA_WARPS)
-    inverse_axpy_kernel(int n, int bw, const double* __restrict__ Lg, const double* __restrict__ invL,
+    inverse_axpy_kernel(int n, int bw, const double* __restrict__ Lsc, const double* __restrict__ invL,
                         double* __restrict__ Kinv) {
   extern __shared__ double dyn[];
   constexpr int WIN = 32 * NS;
   const int W = bw + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double* L = Lg;
+  const double* Lc = Lsc;                    // L_rk / L_kk
+  const double* Lr = Lsc + (size_t)n * W;   // L_ir / L_ii
+  const double* L = Lc;
   if (LSMEM) {
-    for (int q = threadIdx.x; q < n * W; q += blockDim.x) dyn[q] = Lg[q];
+    for (int q = threadIdx.x; q < n * W; q += blockDim.x) dyn[q] = Lc[q];
     L = dyn;
   }
   double* ybuf = dyn + (LSMEM ? (size_t)n * W : 0) + (size_t)warp * n;
   __syncthreads();
   const int j = blockIdx.x * INVA_WARPS + warp;
-  if (j >= n) return;  // no block-level synchronisation below
+  const bool active = j < n;  // the block's barriers below involve every warp
   double acc[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) acc[s] = 0.0;
@@ -595,35 +609,47 @@ __global__ void __launch_bounds__(32 * INVA_WARPS)
     }
     return v;
   };
-  for (int k = j; k < n; ++k) {
-    const double il = invL[k];
-    const double ak = take(k);
-    const double y = k == j ? fma(-ak, il, il) : -ak * il;
-    if (lane == 0) ybuf[k] = y;
+  if (active) {
+    for (int k = j; k < n; ++k) {
+      const double ak = take(k);
+      const double yh = k == j ? 1.0 - ak : -ak;
+      if (lane == 0) ybuf[k] = yh;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int o = (lane + 32 * s - (k + 1)) & (WIN - 1);  // row k + 1 + o
-      const int r = k + 1 + o;
-      if (o < bw && r < n) acc[s] = fma(L[(size_t)r * W + 1 + o], y, acc[s]);
+      for (int s = 0; s < NS; ++s) {
+        const int o = (lane + 32 * s - (k + 1)) & (WIN - 1);  // row k + 1 + o
+        const int r = k + 1 + o;
+        if (o < bw && r < n) acc[s] = fma(L[(size_t)r * W + 1 + o], yh, acc[s]);
+      }
     }
+    __syncwarp();
+    for (int k = j + lane; k < n; k += 32) ybuf[k] *= invL[k];
+    __syncwarp();
   }
-  __syncwarp();
+  if (LSMEM) {  // the factor scaled by its rows' pivots for the backward pass
+    __syncthreads();
+    for (int q = threadIdx.x; q < n * W; q += blockDim.x) dyn[q] = Lr[q];
+    __syncthreads();
+  } else {
+    L = Lr;
+  }
+  if (!active) return;
 #pragma unroll
   for (int s = 0; s < NS; ++s) acc[s] = 0.0;
   double* row = Kinv + (size_t)j * n;
   for (int i = n - 1; i >= 0; --i) {
-    const double il = invL[i];
     const double yi = i >= j ? ybuf[i] : 0.0;
     const double ai = take(i);
-    const double x = (yi - ai) * il;
-    if (lane == 0) row[i] = x;
+    const double xh = yi - ai;  // x_i L_ii
+    if (lane == 0) row[i] = xh;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const int o = ((i - 1) - (lane + 32 * s)) & (WIN - 1);  // row i - 1 - o
       const int r = i - 1 - o;
-      if (o < bw && r >= 0) acc[s] = fma(L[(size_t)i * W + 1 + o], x, acc[s]);
+      if (o < bw && r >= 0) acc[s] = fma(L[(size_t)i * W + 1 + o], xh, acc[s]);
     }
   }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) row[i] *= invL[i];
 }
 
 struct CholPlan {
@@ -679,25 +705,25 @@ cudaError_t prepare_cholesky_inverse(int n, int bw) {
   return e;
 }
 
-cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Kinv,
+cudaError_t launch_cholesky_inverse(int n, int bw, double* Kb, double* invL, double* Lsc, double* Kinv,
                                     int* err_flag, cudaStream_t s, int num_sms) {
   (void)num_sms;
   const CholPlan pl = chol_plan(n, bw);
   if (pl.band_smem)
-    cholesky_band_kernel<true><<<1, CHOL_NT, pl.band + pl.pairs, s>>>(n, bw, Kb, invL, err_flag);
+    cholesky_band_kernel<true><<<1, CHOL_NT, pl.band + pl.pairs, s>>>(n, bw, Kb, invL, Lsc, err_flag);
   else
-    cholesky_band_kernel<false><<<1, CHOL_NT, pl.pairs, s>>>(n, bw, Kb, invL, err_flag);
+    cholesky_band_kernel<false><<<1, CHOL_NT, pl.pairs, s>>>(n, bw, Kb, invL, Lsc, err_flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (pl.slots) {
     const int ab = (n + INVA_WARPS - 1) / INVA_WARPS;
     const size_t sm = (pl.axpy_smem ? pl.band : 0) + pl.ybuf;
     if (pl.slots == 2) {
-      if (pl.axpy_smem) inverse_axpy_kernel<true, 2><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
-      else inverse_axpy_kernel<false, 2><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
+      if (pl.axpy_smem) inverse_axpy_kernel<true, 2><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Lsc, invL, Kinv);
+      else inverse_axpy_kernel<false, 2><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Lsc, invL, Kinv);
     } else {
-      if (pl.axpy_smem) inverse_axpy_kernel<true, 4><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
-      else inverse_axpy_kernel<false, 4><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Kb, invL, Kinv);
+      if (pl.axpy_smem) inverse_axpy_kernel<true, 4><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Lsc, invL, Kinv);
+      else inverse_axpy_kernel<false, 4><<<ab, 32 * INVA_WARPS, sm, s>>>(n, bw, Lsc, invL, Kinv);
     }
     return cudaGetLastError();
   }
