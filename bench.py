@@ -43,7 +43,7 @@ SMOOTH64_OPS_PER_NODE = 38  # K v 32, w D^-1 b 2, z + d (b - K v) 4 (first two s
 # dram__bytes_write.sum, profiles/sweeps_2048_ncu_full.md); None once the
 # kernel changes.
 KP_TRAFFIC = 354_025_984
-SMOOTH32_TRAFFIC = 248_203_264
+SMOOTH32_TRAFFIC = 249_000_704
 # FP64 pipe: 2 operations per clock per SM (1.25 TFLOP/s nominal at 2 flops
 # per FMA), 152 SMs, 2070 MHz.
 FP64_OPS_PEAK = 2 * 152 * 2.070e9
