@@ -550,6 +550,14 @@ __device__ __forceinline__ void sweep2_warp(const SweepParams<T>& a, int wg, int
             prefetch_l2(a.q64 + k + (PF + 2) * pitch);
           }
         }
+        if constexpr (FBF && MODE == MODE_RESTRICT) {
+          if (je + PF + 2 <= je1) {  // marched vector, b and moduli beyond the ring
+            const long long kp = k + (PF + 2) * pitch;
+            prefetch_l2(a.v + kp);
+            prefetch_l2(a.b + kp);
+            prefetch_l2(static_cast<const __nv_bfloat16*>(a.E) + kp);
+          }
+        }
 
         // ---- top row je + 1 ----
         T2 vt0, vt1;
