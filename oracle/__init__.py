@@ -14,7 +14,7 @@ primitives):
   * cholesky     -- Alg. 3 (dense Cholesky) with forward/back substitution.
   * multigrid    -- bilinear prolongation P and R = P^T (Sec. 2.1), Galerkin
                     and rediscretised coarse operators, damped Jacobi (Sec. 2.3),
-                    the gamma-cycle of Alg. 1 with gamma = 1.
+                    the gamma-cycle of Alg. 1 (V- and W-cycle).
   * pcg          -- Alg. 2 (preconditioned conjugate gradient).
   * sensitivity  -- compliance C = f.u (Eq. 6) and the self-adjoint
                     sensitivity dC/dx_{e,i} = -p x^{p-1} E_i u_e^T KE u_e.

@@ -15,9 +15,12 @@ Readings (the paper does not fix these):
     the four child moduli (Sec. 2.1 speaks of a discretisation on each mesh).
   * A coarse node is clamped exactly when it lies on a clamped edge; all
     operators act on the free DOFs only.
-  * gamma = 1 on every level (a V-cycle); the smoother is damped Jacobi with
-    nu1 pre- and nu2 post-sweeps, the coarsest system is solved by the dense
-    Cholesky factorisation of Alg. 3.
+  * The finest level calls the next coarser grid once and every other level
+    calls it gamma times (Alg. 1 sets gamma = 1 on the finest grid): gamma = 1
+    is the V-cycle, gamma = 2 the W-cycle.  Each repeated call starts from the
+    coarse iterate that the previous one returned.  The smoother is damped
+    Jacobi with nu1 pre- and nu2 post-sweeps; the coarsest system is solved by
+    the dense Cholesky factorisation of Alg. 3.
 """
 
 import numpy as np
@@ -125,8 +128,9 @@ def mg_cycle(levels, l, U, F, omega, nu1, nu2, gamma=1):
 
     l == 0: U = K_0^-1 F (Cholesky, Alg. 3).  Otherwise: pre-smooth nu1 times,
     restrict the residual F_{l-1} = R_l (F_l - K_l U_l), start the coarse
-    iterate at zero, call the scheme gamma times on level l-1, correct with
-    U_l += P_l U_{l-1}, post-smooth nu2 times.
+    iterate at zero, call the scheme on level l-1 (once when l is the finest
+    level, gamma times otherwise), correct with U_l += P_l U_{l-1},
+    post-smooth nu2 times.
     """
     lev = levels[l]
     if l == 0:
@@ -134,18 +138,20 @@ def mg_cycle(levels, l, U, F, omega, nu1, nu2, gamma=1):
     U = damped_jacobi(lev.K, lev.diag, U, F, omega, nu1)
     Fc = lev.P.T @ (F - lev.K @ U)
     Uc = np.zeros(levels[l - 1].n_free)
-    for _ in range(gamma):
+    calls = 1 if l == len(levels) - 1 else gamma
+    for _ in range(calls):
         Uc = mg_cycle(levels, l - 1, Uc, Fc, omega, nu1, nu2, gamma)
     U = U + lev.P @ Uc
     return damped_jacobi(lev.K, lev.diag, U, F, omega, nu2)
 
 
-def vcycle_preconditioner(levels, omega=0.6, nu1=2, nu2=2):
-    """z = M^-1 r: one V-cycle on the finest level started from U = 0 (Sec. 2.2)."""
+def vcycle_preconditioner(levels, omega=0.6, nu1=2, nu2=2, gamma=1):
+    """z = M^-1 r: one cycle of Alg. 1 on the finest level started from U = 0
+    (Sec. 2.2); a V-cycle for gamma = 1, a W-cycle for gamma = 2."""
     L = len(levels) - 1
 
     def apply(r):
-        return mg_cycle(levels, L, np.zeros_like(r), r, omega, nu1, nu2, gamma=1)
+        return mg_cycle(levels, L, np.zeros_like(r), r, omega, nu1, nu2, gamma)
 
     return apply
 

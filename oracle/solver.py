@@ -22,8 +22,9 @@ def solve_direct(nelx, nely, x, E_phase, penal, f, nu=0.3, fixed_edges=fem.BOTTO
 def solve_pcgmg(nelx, nely, x, E_phase, penal, f, nu=0.3, fixed_edges=fem.BOTTOM,
                 n_coarsen=3, omega=0.6, nu1=2, nu2=2, tol=1e-10, max_it=1000,
                 coarse_kind="galerkin", u0=None, flexible=False, rr_every=0,
-                vcycle_E=None):
-    """PCG (Alg. 2) with a V-cycle (Alg. 1) preconditioner.
+                vcycle_E=None, gamma=1):
+    """PCG (Alg. 2) preconditioned by one cycle of Alg. 1 (gamma = 1: V-cycle,
+    2: W-cycle).
 
     vcycle_E, when given, replaces the element moduli inside the preconditioner
     only (the mixed-precision path builds its V-cycle from bfloat16 moduli while
@@ -43,7 +44,7 @@ def solve_pcgmg(nelx, nely, x, E_phase, penal, f, nu=0.3, fixed_edges=fem.BOTTOM
         K = fem.assemble(nelx, nely, E, KE)[free][:, free]
     f_full = np.asarray(f, dtype=np.float64).ravel()
     x0 = None if u0 is None else np.asarray(u0, dtype=np.float64).ravel()[free]
-    M = multigrid.vcycle_preconditioner(levels, omega, nu1, nu2)
+    M = multigrid.vcycle_preconditioner(levels, omega, nu1, nu2, gamma)
     uf, iters, conv, hist = pcg.pcg(lambda v: K @ v, f_full[free], M, x0=x0, tol=tol,
                                     max_it=max_it, flexible=flexible, rr_every=rr_every)
     u = np.zeros_like(f_full)

@@ -164,6 +164,72 @@ def test_vcycle_unsymmetric_smoothing_breaks_symmetry():
     assert abs(a @ M(b) - b @ M(a)) > 1e-6 * abs(a @ M(b))
 
 
+def _cycle_error_operator(lv, omega, nu1, nu2, gamma):
+    """Error propagation of Alg. 1, built from matrices level by level:
+    E_0 = 0 and E_l = S_l^nu2 (I - P_l (I - E_{l-1}^c) K_{l-1}^-1 P_l^T K_l) S_l^nu1,
+    S_l = I - omega D_l^-1 K_l, with c = 1 on the finest level and gamma below
+    it (gamma calls on level l-1, each continuing from the last iterate)."""
+    E_prev = np.zeros((lv[0].n_free, lv[0].n_free))
+    for l in range(1, len(lv)):
+        K, P, Kc = lv[l].K.toarray(), lv[l].P.toarray(), lv[l - 1].K.toarray()
+        n = K.shape[0]
+        S = np.eye(n) - omega * K / np.diag(K)[:, None]
+        c = 1 if l == len(lv) - 1 else gamma
+        inner = np.eye(Kc.shape[0]) - np.linalg.matrix_power(E_prev, c)
+        T = np.eye(n) - P @ inner @ np.linalg.solve(Kc, P.T @ K)
+        E_prev = np.linalg.matrix_power(S, nu2) @ T @ np.linalg.matrix_power(S, nu1)
+    return E_prev
+
+
+@pytest.mark.parametrize("gamma", [1, 2, 3])
+def test_gamma_cycle_matches_error_propagation(gamma):
+    # Four grids (16^2 down to 2^2): the W-cycle visits the 4^2 grid twice
+    # and the coarsest four times, each visit from the last coarse iterate.
+    nelx, nely = 16, 16
+    E = design_E(nelx, nely, 12)
+    lv = multigrid.build_hierarchy(nelx, nely, E, fem.element_stiffness(0.3), BOTTOM, 3)
+    rng = np.random.default_rng(13)
+    n = lv[-1].n_free
+    U0, F = rng.standard_normal(n), rng.standard_normal(n)
+    Us = np.linalg.solve(lv[-1].K.toarray(), F)
+    Em = _cycle_error_operator(lv, 0.6, 2, 1, gamma)
+    U = multigrid.mg_cycle(lv, len(lv) - 1, U0, F, 0.6, 2, 1, gamma)
+    np.testing.assert_allclose(U - Us, Em @ (U0 - Us), atol=1e-9 * np.abs(Us).max())
+
+
+def test_w_cycle_equals_v_cycle_on_three_grids_only():
+    # Alg. 1 calls the next grid once from the finest grid, and a repeated
+    # exact coarsest solve returns the same iterate: with two or three grids
+    # the W-cycle is the V-cycle; from four grids on it is not.
+    nelx, nely = 16, 16
+    E = design_E(nelx, nely, 14)
+    KE = fem.element_stiffness(0.3)
+    r = np.random.default_rng(15).standard_normal
+    for nc in (1, 2):
+        lv = multigrid.build_hierarchy(nelx, nely, E, KE, BOTTOM, nc)
+        b = r(lv[-1].n_free)
+        np.testing.assert_array_equal(multigrid.vcycle_preconditioner(lv, gamma=2)(b),
+                                      multigrid.vcycle_preconditioner(lv)(b))
+    lv = multigrid.build_hierarchy(nelx, nely, E, KE, BOTTOM, 3)
+    b = r(lv[-1].n_free)
+    zv = multigrid.vcycle_preconditioner(lv)(b)
+    zw = multigrid.vcycle_preconditioner(lv, gamma=2)(b)
+    assert np.linalg.norm(zw - zv) > 1e-3 * np.linalg.norm(zv)
+
+
+def test_w_cycle_is_symmetric_positive_definite():
+    nelx, nely = 16, 16
+    E = design_E(nelx, nely, 16)
+    lv = multigrid.build_hierarchy(nelx, nely, E, fem.element_stiffness(0.3), BOTTOM, 3)
+    M = multigrid.vcycle_preconditioner(lv, gamma=2)
+    rng = np.random.default_rng(17)
+    n = lv[-1].n_free
+    for _ in range(3):
+        a, b = rng.standard_normal(n), rng.standard_normal(n)
+        assert a @ M(b) == pytest.approx(b @ M(a), rel=1e-11)
+        assert a @ M(a) > 0
+
+
 def test_pcg_without_preconditioner_matches_textbook_cg():
     rng = np.random.default_rng(5)
     A = rng.standard_normal((30, 30)); A = A @ A.T + 30 * np.eye(30)
@@ -190,6 +256,18 @@ def test_pcgmg_converges_to_direct_solution(n_coarsen, kind):
     err = np.linalg.norm(res["u"] - ud) / np.linalg.norm(ud)
     assert err < 1e-8
     assert np.all(res["u"][0] == 0.0)
+
+
+def test_pcgmg_with_w_cycle_converges_to_direct_solution():
+    nelx, nely = 32, 32
+    x = dirichlet_design(nelx, nely, 4, seed=3)
+    f = load_top_edge(nelx, nely)
+    ud = solver.solve_direct(nelx, nely, x, EP, 3.0, f)
+    rv = solver.solve_pcgmg(nelx, nely, x, EP, 3.0, f, n_coarsen=4, tol=1e-12)
+    rw = solver.solve_pcgmg(nelx, nely, x, EP, 3.0, f, n_coarsen=4, tol=1e-12, gamma=2)
+    assert rw["converged"]
+    assert np.linalg.norm(rw["u"] - ud) / np.linalg.norm(ud) < 1e-8
+    assert rw["iters"] != rv["iters"] or not np.array_equal(rw["history"], rv["history"])
 
 
 def test_pcgmg_flexible_and_replacement_and_warm_start():
