@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--n-coarsen", type=int, default=7)
+    ap.add_argument("--gamma", type=int, default=1, help="cycle index of Alg. 1 (1: V, 2: W)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -158,13 +159,13 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle import solver
 from synth import dirichlet_design, load_top_edge
-n, nc, budget, reps = {n}, {nc}, {budget}, {reps}
+n, nc, budget, reps, gamma = {n}, {nc}, {budget}, {reps}, {gamma}
 x = dirichlet_design(n, n, 4, {seed}); f = load_top_edge(n, n)
 times, iters = [], []
 t_all = time.perf_counter()
 while True:
     t = time.perf_counter()
-    r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol=1e-8)
+    r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol=1e-8, gamma=gamma)
     times.append(time.perf_counter() - t); iters.append(r["iters"])
     if (reps and len(times) >= reps) or (not reps and time.perf_counter() - t_all >= budget):
         break
@@ -172,10 +173,10 @@ print(json.dumps({{"times": times, "iters": iters}}))
 """
 
 
-def oracle_sample(n, reps=0, budget=10.0):
+def oracle_sample(n, reps=0, budget=10.0, gamma=1):
     nc = max(1, n.bit_length() - 1 - 4)  # coarsest 16 x 16, as at 2048^2 with 7 coarsenings
     code = ORACLE_SNIPPET.format(root=ROOT, n=n, nc=nc, budget=budget, reps=reps, seed=SEED, ep=EP,
-                                 penal=PENAL)
+                                 penal=PENAL, gamma=gamma)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     d = json.loads(out.stdout.strip().splitlines()[-1])
@@ -217,8 +218,8 @@ def run_reference(args):
         return 0
     n_full, n_s = args.size, args.sample_size
     for _ in range(args.warmup):
-        oracle_sample(n_s, reps=1)
-    d = oracle_sample(n_s, reps=max(1, args.steps))
+        oracle_sample(n_s, reps=1, gamma=args.gamma)
+    d = oracle_sample(n_s, reps=max(1, args.steps), gamma=args.gamma)
     v = cpu_value(d, n_s, n_full)
     ms = 1000.0 * sum(d["times"]) / len(d["times"])
     sample = (f"oracle pCGMG (numpy/scipy, FP64, 1 thread) on {n_s}x{n_s} (nc={d['nc']}), "
@@ -228,7 +229,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"pCGMG {n_full}x{n_full} Q4 square wall (oracle sample {n_s}^2)",
-                   "iters": d["iters"]},
+                   "iters": d["iters"], "gamma": args.gamma},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -412,7 +413,7 @@ def run_ours(args):
         mesh.set_kernel_timing(False)
         return {"ms": t, "samples": cnt}
 
-    common = dict(n_coarsen=nc, tol=1e-8, max_it=1000, device=local)
+    common = dict(n_coarsen=nc, tol=1e-8, max_it=1000, gamma=args.gamma, device=local)
     mixed = mto.Mesh(n, n, precision="mixed", rr_every=25, flexible=True, **common)
     mixed.set_design(x, EP, PENAL)
     shapes_mixed = [mixed.launch_shape(l) for l in range(nc + 1)] if args.no_tune else mixed.autotune()
@@ -498,7 +499,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        d = oracle_sample(args.sample_size, budget=10.0)
+        d = oracle_sample(args.sample_size, budget=10.0, gamma=args.gamma)
         cpu = {"value": cpu_value(d, args.sample_size, n), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": (f"oracle pCGMG (numpy/scipy FP64, 1 thread) on {args.sample_size}^2, "
                           f"{len(d['times'])} solves ({sum(d['times']):.1f} s), iters {d['iters'][0]}, "
@@ -512,6 +513,7 @@ def run_ours(args):
                                f"Dirichlet fractions), {nc} coarsenings to 16x16, tol 1e-8; step = "
                                "set_design + solve + compliance/sensitivities",
                    "nelx": n, "nely": n, "dofs": ndof(n), "n_coarsen": nc, "precision": "mixed",
+                   "gamma": args.gamma,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (design 134 MB + load 67 MB read every step)"},
         "gdof_iter_s": gdof, "gdof_iter_s_solve_only": gdof_solve, "iters": iters,

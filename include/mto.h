@@ -71,6 +71,9 @@ typedef struct {
   int rr_every;     /* mixed path: replace r by f - K u every k iterations (0: never) */
   int flexible;     /* 1: flexible (Polak-Ribiere) beta, 0: Fletcher-Reeves as in Alg. 2 */
   int check_every;  /* host convergence poll interval in iterations (>= 1) */
+  int gamma;        /* cycle index of Alg. 1 below the finest grid, 1..4 (1: V-cycle,
+                       2: W-cycle); the finest grid calls the next one once.  At most
+                       512 coarse-grid calls per cycle (MTO_ERR_ARG otherwise). */
 } mto_solver_opts;
 
 typedef struct {
@@ -83,7 +86,7 @@ typedef struct {
 } mto_solve_stats;
 
 /* Fills the defaults: tol 1e-8, max_it 500, omega 0.6, nu1 = nu2 = 2,
- * n_coarsen 3, Galerkin, FP64, rr_every 25, flexible 0, check_every 4. */
+ * n_coarsen 3, Galerkin, FP64, rr_every 25, flexible 0, check_every 4, gamma 1. */
 void mto_default_opts(mto_solver_opts* opts);
 
 /* Creates a context for an nelx x nely mesh with Poisson ratio nu and the

@@ -43,6 +43,7 @@ class SolverOpts(ctypes.Structure):
         ("rr_every", ctypes.c_int),
         ("flexible", ctypes.c_int),
         ("check_every", ctypes.c_int),
+        ("gamma", ctypes.c_int),
     ]
 
 

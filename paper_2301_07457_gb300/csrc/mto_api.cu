@@ -107,10 +107,15 @@ template <typename T> void set_cfine(const mto_ctx* c, SweepParams<T>& p) {
   p.redisc = c->o.coarse_kind == MTO_COARSE_REDISCRETIZE;
 }
 
-// One V-cycle (Alg. 1) on coarse level l >= 1 with right-hand side lv[l].b.
-// Returns the index of the z buffer that holds the result.
+template <typename T> mto_status coarse_calls(mto_ctx* c, int l, int calls, DevScalars* sc,
+                                               int* final_idx);
+
+// One call MG^l(U_l, F_l) of Alg. 1 on coarse level l >= 1 with right-hand
+// side lv[l].b: from U_l = 0 when start < 0, else from the iterate in
+// lv[l].z[start] (the repeated calls of a W-cycle).  Returns the index of the
+// z buffer that holds the result.
 template <typename T>
-mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
+mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int start, int* final_idx) {
   using T2 = typename V2<T>::t;
   LevelBuf& L = c->lv[l];
   LevelBuf& C = c->lv[l - 1];
@@ -143,7 +148,14 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
   // float32 level, the residual and its restriction run in the same pass
   // (mto_fused.cuh).
   const bool fused_pre = (src == SRC_CMOM || src == SRC_CFINE) && c->o.nu1 == 2;
-  if (fused_pre) {
+  if (start >= 0) {
+    cur = start;
+    for (int s = 0; s < c->o.nu1; ++s) {
+      KL(sweep(MODE_SMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], nullptr));
+      cur ^= 1;
+    }
+    KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
+  } else if (fused_pre) {
     KL(sweep(MODE_PRE2, nullptr, (T2*)L.z[0], nullptr));
   } else {
     if (c->o.nu1 >= 2) {
@@ -159,12 +171,7 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr));
   }
   int cidx = 0;
-  if (l - 1 == 0) {
-    KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
-                               (T2*)C.z[0], sc, c->cs));
-  } else {
-    ST(coarse_cycle<T>(c, l - 1, sc, &cidx));
-  }
+  ST(coarse_calls<T>(c, l - 1, c->o.gamma, sc, &cidx));
   // Post-smoothing; on the float32 levels the prolongation sweep and the
   // next one run fused (mto_fused.cuh).
   int s = 1;
@@ -180,6 +187,26 @@ mto_status coarse_cycle(mto_ctx* c, int l, DevScalars* sc, int* final_idx) {
     cur ^= 1;
   }
   *final_idx = cur;
+  return MTO_OK;
+}
+
+// "Call the scheme gamma times for the next coarser grid" (Alg. 1) on level
+// l, each call continuing from the iterate the previous one returned.  On
+// the coarsest grid the scheme is the exact solve U_0 = K_0^-1 F_0, which
+// does not depend on the iterate: one GEMV stands for all calls.
+template <typename T>
+mto_status coarse_calls(mto_ctx* c, int l, int calls, DevScalars* sc, int* final_idx) {
+  using T2 = typename V2<T>::t;
+  if (l == 0) {
+    LevelBuf& C = c->lv[0];
+    KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
+                               (T2*)C.z[0], sc, c->cs));
+    *final_idx = 0;
+    return MTO_OK;
+  }
+  int idx = -1;
+  for (int k = 0; k < calls; ++k) ST(coarse_cycle<T>(c, l, sc, idx, &idx));
+  *final_idx = idx;
   return MTO_OK;
 }
 
@@ -272,13 +299,9 @@ mto_status fine_cycle(mto_ctx* c, DevScalars* sc, bool with_dot, int* final_idx)
     cur ^= 1;
   }
   KL(sweep(MODE_RESTRICT, (const T2*)L.z[cur], nullptr, nullptr, false));
+  // Alg. 1 calls the next coarser grid once from the finest grid.
   int cidx = 0;
-  if (c->L - 1 == 0) {
-    KL(launch_coarsest_gemv<T>(C.g, c->n0, c->dof_index + 2 * C.g.size(), c->Kinv, (const T2*)C.b,
-                               (T2*)C.z[0], sc, c->cs));
-  } else {
-    ST(coarse_cycle<T>(c, c->L - 1, sc, &cidx));
-  }
+  ST(coarse_calls<T>(c, c->L - 1, 1, sc, &cidx));
   KL(sweep(MODE_PSMOOTH, (const T2*)L.z[cur], (T2*)L.z[cur ^ 1], (const T2*)C.z[cidx],
            with_dot && c->o.nu2 == 1));
   cur ^= 1;
@@ -452,12 +475,24 @@ mto_status solve_polled(mto_ctx* c) {
   return MTO_OK;
 }
 
+// Coarse-level calls of one cycle below the finest level (the coarsest grid
+// excluded): once on the next grid, gamma times on the one below, and so on.
+// Each call adds a few kernels to the solve graph, so the count is capped.
+constexpr long MAX_COARSE_VISITS = 512;
+long coarse_visits(int n_coarsen, int gamma) {
+  long visits = 0, per = 1;
+  for (int l = n_coarsen - 1; l >= 1 && visits <= MAX_COARSE_VISITS; --l, per *= gamma)
+    visits += per;
+  return visits;
+}
+
 bool valid_opts(const mto_solver_opts& o) {
   return o.tol >= 0.0 && o.max_it >= 0 && o.omega > 0.0 && o.omega <= 1.0 && o.nu1 >= 1 &&
          o.nu2 >= 1 && o.nu1 <= 16 && o.nu2 <= 16 && o.n_coarsen >= 1 && o.n_coarsen <= 14 &&
          (o.coarse_kind == MTO_COARSE_GALERKIN || o.coarse_kind == MTO_COARSE_REDISCRETIZE) &&
          (o.precision == MTO_PRECISION_FP64 || o.precision == MTO_PRECISION_MIXED) &&
-         o.rr_every >= 0 && o.check_every >= 1;
+         o.rr_every >= 0 && o.check_every >= 1 && o.gamma >= 1 && o.gamma <= 4 &&
+         coarse_visits(o.n_coarsen, o.gamma) <= MAX_COARSE_VISITS;
 }
 
 mto_status status_of(const RhsStats& r) {
@@ -741,6 +776,7 @@ void mto_default_opts(mto_solver_opts* o) {
   o->rr_every = 25;
   o->flexible = 0;
   o->check_every = 4;
+  o->gamma = 1;
 }
 
 const char* mto_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }

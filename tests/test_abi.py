@@ -47,6 +47,7 @@ def test_library_loads_and_binding_matches(libpath):
     assert lib.mto_status_string(5) == b"not converged"
     o = _lib.default_opts()
     assert (o.tol, o.max_it, o.omega, o.nu1, o.nu2, o.n_coarsen) == (1e-8, 500, 0.6, 2, 2, 3)
+    assert o.gamma == 1
 
 
 def test_argument_validation_needs_no_gpu(libpath):
@@ -62,5 +63,12 @@ def test_argument_validation_needs_no_gpu(libpath):
         _lib.ERR_UNSUPPORTED_MESH
     o.omega = 1.5
     assert lib.mto_create_mesh(ctypes.byref(h), 8, 8, 0.3, 1, ctypes.byref(o), 0, None) == _lib.ERR_ARG
+    # Cycle index: 1..4, and at most 512 coarse-grid calls per cycle
+    # (gamma = 3 with 8 coarsenings makes 1093).
+    o.omega = 0.6
+    for gamma, nc in ((0, 3), (5, 3), (3, 8)):
+        o.gamma, o.n_coarsen = gamma, nc
+        assert lib.mto_create_mesh(ctypes.byref(h), 512, 512, 0.3, 1, ctypes.byref(o), 0,
+                                   None) == _lib.ERR_ARG, (gamma, nc)
     assert lib.mto_solve(None, 1, None, None, None) == _lib.ERR_ARG
     assert lib.mto_create_mesh(None, 8, 8, 0.3, 1, None, 0, None) == _lib.ERR_ARG
