@@ -67,6 +67,11 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (for profiling)")
     ap.add_argument("--sweep-outer", type=int, default=50)
+    ap.add_argument("--study", choices=["levels"], default=None,
+                    help="instead of the bench line: pCGMG level study on the paper's meshes")
+    ap.add_argument("--study-precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--study-outer", type=int, default=100,
+                    help="level study: most outer optimiser iterations per mesh and level")
     return ap.parse_args()
 
 
@@ -532,8 +537,78 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Level study (Sec. 5.2, Tables 2-5): pCGMG with l = 2 ... 6 grids on the
+# paper's meshes, Table 2's parameters
+# ---------------------------------------------------------------------------
+PAPER_MESHES = ((32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (128, 256))
+TABLE2 = {"E": [9.0, 3.0, 1.0, 1e-9], "V": [0.16, 0.08, 0.08, 0.68], "penal": 3.0, "rf": 8.0,
+          "tol": 1e-3, "cgtol": 1e-6, "cgmax": 1000}
+
+
+def run_level_study(args):
+    """One JSON line per (mesh, l): a cold set_design + solve on the seeded
+    design with Table 2's moduli (device time, median of args.steps), then the
+    outer optimiser loop of Sec. 4 from the uniform design until no fraction
+    moves by more than Table 2's tol (at most args.study_outer outer
+    iterations, wall time).  Meshes are nelx x nely as printed; l counts the
+    grids (l = 2 is the two-level method), so n_coarsen = l - 1."""
+    import torch
+
+    from paper_2301_07457_gb300.build import build
+    build()
+    import paper_2301_07457_gb300 as mto
+    from paper_2301_07457_gb300 import MtoError
+    from paper_2301_07457_gb300.optimize import ActivePhaseOptimizer
+    from synth import dirichlet_design, load_top_edge
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    T = TABLE2
+    for nelx, nely in PAPER_MESHES:
+        f = torch.from_numpy(load_top_edge(nelx, nely)).to(dev)
+        x = torch.from_numpy(dirichlet_design(nelx, nely, 4, SEED)).to(dev)
+        for l in range(2, 7):
+            row = {"study": "levels", "mesh": f"{nelx}x{nely}", "l": l, "n_coarsen": l - 1,
+                   "coarsest": f"{nelx >> (l - 1)}x{nely >> (l - 1)}", "precision": args.study_precision}
+            try:
+                mesh = mto.Mesh(nelx, nely, n_coarsen=l - 1, precision=args.study_precision,
+                                tol=T["cgtol"], max_it=T["cgmax"], device=0)
+            except MtoError as e:
+                row["unsupported"] = str(e)
+                print(json.dumps(row), flush=True)
+                continue
+            row["coarsest_free_dofs"] = mesh.info()["coarsest_free_dofs"]
+            ms = []
+            for rep in range(args.warmup + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mesh.set_design(x, T["E"], T["penal"])
+                u, st = mesh.solve(f, raise_on_failure=False)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+            row["solve"] = {"iters": st["iters"], "status": st["status"], "ms": sorted(ms)[len(ms) // 2],
+                            "ms_setup": st["ms_setup"], "ms_solve": st["ms_solve"]}
+            opt = ActivePhaseOptimizer(mesh, T["E"], T["V"], f, penal=T["penal"], rf=T["rf"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            met = opt.run_until(T["tol"], args.study_outer)
+            torch.cuda.synchronize()
+            its = [h[3] for h in opt.history]
+            row["optimiser"] = {"outer": opt.iteration, "stopped_by_tol": met, "solves": len(its),
+                                "pcg_iters_mean": sum(its) / len(its), "pcg_iters_max": max(its),
+                                "seconds": time.perf_counter() - t0, "compliance": opt.history[-1][2]}
+            mesh.close()
+            print(json.dumps(row), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.study == "levels":
+        return run_level_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -83,11 +83,14 @@ class Level:
         return self.free.size
 
 
-def build_hierarchy(nelx, nely, E, KE, fixed_edges, n_coarsen, coarse_kind="galerkin"):
+def build_hierarchy(nelx, nely, E, KE, fixed_edges, n_coarsen, coarse_kind="galerkin",
+                    factor_coarsest=True):
     """Return [level_0 (coarsest), ..., level_L (finest)].
 
     The finest operator is the assembled K of Eq. 7 restricted to the free DOFs.
     coarse_kind: "galerkin" (K_c = P^T K P) or "rediscretize" (mean child E).
+    factor_coarsest=False skips the dense Cholesky factor of level 0 (Alg. 3,
+    cubic in its size) for callers that only need the operators.
     """
     if nelx % (1 << n_coarsen) or nely % (1 << n_coarsen):
         raise ValueError("mesh must be divisible by 2**n_coarsen")
@@ -112,7 +115,7 @@ def build_hierarchy(nelx, nely, E, KE, fixed_edges, n_coarsen, coarse_kind="gale
         fine.P = P
         levels.append(Level(ncx, ncy, free_c, Kc, Ec))
     levels.reverse()
-    levels[0].chol = cholesky.cholesky(levels[0].K.toarray())
+    levels[0].chol = cholesky.cholesky(levels[0].K.toarray()) if factor_coarsest else None
     return levels
 
 

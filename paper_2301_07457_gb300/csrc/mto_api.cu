@@ -915,7 +915,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
           inv.push_back((int)(2 * g0.at(i, j) + comp));
         }
   c->n0 = (int)inv.size();
-  if (c->n0 > 4096) return MTO_ERR_UNSUPPORTED_MESH;
+  if (c->n0 > GEMV_MAXN) return MTO_ERR_UNSUPPORTED_MESH;
   int bw = 0;
   for (int j = 0; j <= g0.ny; ++j)
     for (int i = 0; i <= g0.nx; ++i)
@@ -932,6 +932,9 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
           }
       }
   c->bw0 = bw;
+  // The factorisation keeps the (i, j) index pairs of a band triangle in
+  // shared memory (2 bw (bw + 1) bytes).
+  if (bw > MAX_COARSEST_BW) return MTO_ERR_UNSUPPORTED_MESH;
   std::vector<int> dof(2 * (size_t)g0.size() + c->n0);
   std::memcpy(dof.data(), idx.data(), sizeof(int) * 2 * (size_t)g0.size());
   std::memcpy(dof.data() + 2 * (size_t)g0.size(), inv.data(), sizeof(int) * c->n0);
@@ -958,6 +961,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   // Opt-in shared memory of the coarsest factorisation, set once here so that
   // set_design can be captured into graphs.
   CK(prepare_cholesky_inverse(c->n0, c->bw0));
+  CK(prepare_coarsest_gemv(c->n0));
   return MTO_OK;
 }
 

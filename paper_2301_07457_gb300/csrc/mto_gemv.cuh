@@ -7,7 +7,10 @@
 
 namespace mto {
 
-constexpr int GEMV_MAXN = 4096;  // shared-memory staging of b: 32 KiB
+// Largest coarsest system: b is staged in shared memory (132 KiB at the
+// limit; the kernel opts in above 48 KiB), and K_0^-1 takes 8 n^2 bytes
+// (2.3 GB at the limit).
+constexpr int GEMV_MAXN = 16896;
 
 // Every thread of the block: stage b at the free DOFs in shared memory
 // (free_idx[k] = scalar index 2 * node offset + component of free DOF k).

@@ -5,6 +5,7 @@
 #include <utility>
 
 #include "mto_fused.cuh"
+#include "mto_gemv.cuh"
 #include "mto_sweep2.cuh"
 
 namespace mto {
@@ -117,6 +118,9 @@ template <typename T>
 cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, const double* Kinv,
                                  const typename V2<T>::t* b, typename V2<T>::t* z,
                                  DevScalars* sc, cudaStream_t s);
+// Opt-in shared memory of the GEMV for n free coarsest DOFs (b is staged in
+// shared memory: 8 n bytes), once per size, outside any stream capture.
+cudaError_t prepare_coarsest_gemv(int n);
 
 // PCG scalars of a fresh solve; loop condition of the device-side solver loop;
 // per-solve outcome record.
@@ -161,7 +165,10 @@ cudaError_t launch_kmom(const Grid& g, const double* mom, double nu, float* out,
 cudaError_t launch_band_assemble(const Grid& g, const double* coef64, const int* dof_index, int n,
                                  int bw, double* Kb, cudaStream_t s);
 // Opt-in shared memory of the coarsest factorisation kernels (once per size,
-// outside any stream capture).
+// outside any stream capture).  Half-bandwidths up to MAX_COARSEST_BW keep
+// the factorisation's index pairs (2 bw (bw + 1) bytes) and the inverse's
+// ring (256 (bw + 1) bytes) within the opt-in shared memory of a block.
+constexpr int MAX_COARSEST_BW = 320;
 cudaError_t prepare_cholesky_inverse(int n, int bw);
 // In-place band Cholesky of Kb (1 / L_ii to invL; the factor scaled by its
 // columns' and rows' pivots to Lsc, 2 n (bw + 1) doubles), then the explicit

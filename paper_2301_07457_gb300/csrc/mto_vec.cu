@@ -361,6 +361,17 @@ cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, cons
                     reinterpret_cast<const T*>(b), reinterpret_cast<T*>(z),
                     static_cast<const DevScalars*>(sc));
 }
+cudaError_t prepare_coarsest_gemv(int n) {
+  if (n > GEMV_MAXN) return cudaErrorInvalidValue;
+  const int bytes = n * (int)sizeof(double);
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(coarsest_gemv_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(coarsest_gemv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
 template cudaError_t launch_coarsest_gemv<double>(const Grid&, int, const int*, const double*,
                                                   const double2*, double2*, DevScalars*, cudaStream_t);
 template cudaError_t launch_coarsest_gemv<float>(const Grid&, int, const int*, const double*,

@@ -18,7 +18,10 @@ steps below are this library's reading of it:
   * optimality-criteria step with move limit m and damping eta:
     x_a <- clip(x_a (max(0, -d) / lam)^eta, max(eps, x_a - m), min(s - eps, x_a + m)),
     with lam found by bisection (on the device) so that the phase-a volume
-    equals V_a; then x_b = s - x_a.
+    equals V_a; then x_b = s - x_a;
+  * stopping rule (Table 2 gives a tolerance as the optimiser's only stopping
+    criterion): stop after the outer iteration in which no phase fraction of
+    any element changed by more than tol.
 
 The solve and the sensitivities run in libmto; the filter (float32) and the
 OC step are elementwise/convolution tensor operations on the device.  Checkpoints hold the
@@ -102,6 +105,7 @@ class ActivePhaseOptimizer:
         self.pairs = [(a, b) for a in range(n_phase) for b in range(a + 1, n_phase)]
         self.iteration = 0
         self.history = []  # (outer iteration, pair, compliance, PCG iterations)
+        self.change = float("inf")  # largest fraction change of the last outer iteration
 
     def subproblem(self, a, b):
         mesh = self.mesh
@@ -118,9 +122,11 @@ class ActivePhaseOptimizer:
     def step(self):
         """One outer iteration: every pair once; returns the last compliance."""
         C = None
+        x_before = self.x.clone()
         for a, b in self.pairs:
             C, it = self.subproblem(a, b)
             self.history.append((self.iteration, (a, b), C, it))
+        self.change = (self.x - x_before).abs().max().item()
         self.iteration += 1
         return C
 
@@ -129,10 +135,19 @@ class ActivePhaseOptimizer:
             self.step()
         return self.history
 
+    def run_until(self, tol, max_outer):
+        """Outer iterations until one changes no fraction by more than tol, at
+        most max_outer of them; returns whether the rule was met."""
+        for _ in range(max_outer):
+            self.step()
+            if self.change <= tol:
+                return True
+        return False
+
     def state_dict(self):
         return {"x": self.x.cpu(), "u": self.u.cpu(), "iteration": self.iteration,
                 "history": list(self.history), "volumes": self.volumes, "E_phase": self.E_phase,
-                "penal": self.penal}
+                "penal": self.penal, "change": self.change}
 
     def load_state_dict(self, sd):
         dev = self.mesh.device
@@ -140,6 +155,7 @@ class ActivePhaseOptimizer:
         self.u = sd["u"].to(dev)
         self.iteration = sd["iteration"]
         self.history = list(sd["history"])
+        self.change = sd.get("change", float("inf"))
 
     def save(self, path):
         torch.save(self.state_dict(), path)

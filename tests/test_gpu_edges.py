@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import fem, solver
+from oracle import fem, multigrid, solver
 from synth import BOTTOM, LEFT, RIGHT, TOP, dirichlet_design, load_right_edge, load_top_edge
 
 pytestmark = pytest.mark.gpu
@@ -107,7 +107,10 @@ def test_statuses(mto):
 def test_mesh_limits(mto):
     from paper_2301_07457_gb300 import MtoError, _lib
     with pytest.raises(MtoError) as e:
-        mto.Mesh(128, 128, n_coarsen=1)  # coarsest 64 x 64: 8320 free DOFs > 4096
+        mto.Mesh(256, 256, n_coarsen=1)  # coarsest 128 x 128: 33,024 free DOFs > 16,896
+    assert e.value.code == _lib.ERR_UNSUPPORTED_MESH
+    with pytest.raises(MtoError) as e:
+        mto.Mesh(320, 4, n_coarsen=1)  # coarsest 160 x 2: 644 free DOFs, half-bandwidth 325 > 320
     assert e.value.code == _lib.ERR_UNSUPPORTED_MESH
     with pytest.raises(MtoError) as e:
         mto.Mesh(100, 64, n_coarsen=3)
@@ -135,3 +138,44 @@ def test_mixed_rediscretised_and_partial_warm_start(mto):
     assert st_half["iters"] <= st["iters"]
     assert solver.true_relative_residual(nelx, nely, E, f, u_half.cpu().numpy()) <= 1e-8
     m.close()
+
+
+@pytest.mark.parametrize("nelx,nely,n0", [(64, 128, 4224), (128, 128, 8320), (128, 256, 16640)])
+def test_large_coarsest_system(mto, nelx, nely, n0):
+    # One coarsening (the paper's two-level method) on its larger meshes: a
+    # dense coarsest system of up to 16,640 free DOFs (explicit inverse by
+    # columns for half-bandwidths of 128 and more, the GEMV's right-hand side
+    # in opt-in shared memory).  The two-grid cycle is composed here from the
+    # oracle's operators with a sparse direct coarse solve.
+    import scipy.sparse.linalg as sla
+    x = dirichlet_design(nelx, nely, 4, seed=nelx + nely)
+    E = fem.simp_moduli(x, EP, 3.0)
+    m = mto.Mesh(nelx, nely, n_coarsen=1, tol=1e-10)
+    m.set_design(to_dev(x), EP, 3.0)
+    assert m.info()["coarsest_free_dofs"] == n0
+    lv = multigrid.build_hierarchy(nelx, nely, E, fem.element_stiffness(0.3), BOTTOM, 1,
+                                   factor_coarsest=False)
+    K1, K0, P, free = lv[1].K, lv[0].K.tocsc(), lv[1].P, lv[1].free
+    assert K0.shape[0] == n0
+    r = np.random.default_rng(n0).standard_normal((nely + 1, nelx + 1, 2))
+    r[fem.fixed_node_mask(nelx, nely, BOTTOM)] = 0.0
+    rf = r.ravel()[free]
+    U = multigrid.damped_jacobi(K1, lv[1].diag, np.zeros_like(rf), rf, 0.6, 2)
+    U = U + P @ sla.spsolve(K0, P.T @ (rf - K1 @ U))
+    U = multigrid.damped_jacobi(K1, lv[1].diag, U, rf, 0.6, 2)
+    ref = np.zeros(r.size)
+    ref[free] = U
+    z = m.apply_preconditioner(to_dev(r)).cpu().numpy()
+    lmax = sla.eigsh(K0, 1, which="LA", return_eigenvectors=False)[0]
+    lmin = sla.eigsh(K0, 1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+    bar = max(1e-12, 20 * (lmax / lmin) * np.finfo(float).eps)
+    assert rel(z, ref) < bar, (rel(z, ref), lmax / lmin)
+    f = load_top_edge(nelx, nely)
+    u, st = m.solve(to_dev(f))
+    assert rel(u.cpu().numpy(), solver.solve_direct(nelx, nely, x, EP, 3.0, f)) < 1e-7
+    m.close()
+    mm = mto.Mesh(nelx, nely, n_coarsen=1, tol=1e-8, precision="mixed")
+    mm.set_design(to_dev(x), EP, 3.0)
+    u, st = mm.solve(to_dev(f))
+    assert solver.true_relative_residual(nelx, nely, E, f, u.cpu().numpy()) <= 1e-8
+    mm.close()

@@ -44,3 +44,46 @@ def test_oc_update_meets_volume_bounds_and_move_limit():
     d2[0, 0] = -10.0
     new2 = oc_update(xa, s, d2, target)
     assert new2[0, 0] >= new[0, 0] - 1e-12
+
+
+class OracleMesh:
+    """Stands in for Mesh on the CPU: the oracle's direct solve and gradient."""
+
+    def __init__(self, nelx, nely):
+        self.nelx, self.nely, self.device = nelx, nely, torch.device("cpu")
+
+    def set_design(self, x, E_phase, penal):
+        self.x, self.E_phase, self.penal = x.numpy().copy(), list(E_phase), penal
+
+    def solve(self, f, u0=None):
+        from oracle import solver
+        u = solver.solve_direct(self.nelx, self.nely, self.x, self.E_phase, self.penal, f.numpy())
+        return torch.from_numpy(u), {"iters": 0}
+
+    def compliance_grad(self, f, u):
+        from oracle import solver
+        C, g = solver.compliance_and_gradient(self.nelx, self.nely, self.x, self.E_phase,
+                                              self.penal, f.numpy(), u.numpy())
+        return torch.tensor([C]), torch.from_numpy(g)
+
+
+def test_stopping_rule_of_the_outer_loop():
+    # Table 2 moduli and volume fractions on a 12 x 8 wall: the loop stops
+    # after the first outer iteration that moves no fraction by more than tol.
+    from paper_2301_07457_gb300.optimize import ActivePhaseOptimizer
+    from synth import load_top_edge
+    E, V = [9.0, 3.0, 1.0, 1e-9], [0.16, 0.08, 0.08, 0.68]
+    f = torch.from_numpy(load_top_edge(12, 8))
+    opt = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
+    assert opt.run_until(tol=2e-2, max_outer=60)
+    changes = []
+    ref = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
+    for _ in range(opt.iteration):
+        ref.step()
+        changes.append(ref.change)
+    assert changes[-1] <= 2e-2 and all(c > 2e-2 for c in changes[:-1])
+    assert torch.equal(ref.x, opt.x)
+    # A tolerance it cannot meet: exactly max_outer outer iterations.
+    opt2 = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
+    assert not opt2.run_until(tol=-1.0, max_outer=3)
+    assert opt2.iteration == 3 and len(opt2.history) == 18
