@@ -12,12 +12,16 @@ Readings:
     precision.
   * rr_every = k > 0 replaces the recursive residual by b - A x after every k-th
     update (residual replacement); it is not in the paper.
+
+`trace`, when a list, receives one (p_i, q_i = A p_i, beta used for p_i) tuple
+per step; it only records, the arithmetic is the same with or without it.
 """
 
 import numpy as np
 
 
-def pcg(apply_A, b, apply_M, x0=None, tol=1e-10, max_it=1000, flexible=False, rr_every=0):
+def pcg(apply_A, b, apply_M, x0=None, tol=1e-10, max_it=1000, flexible=False, rr_every=0,
+        trace=None):
     """Solve A x = b.  Returns (x, iters, converged, history of ||r||/||b||)."""
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
@@ -40,11 +44,15 @@ def pcg(apply_A, b, apply_M, x0=None, tol=1e-10, max_it=1000, flexible=False, rr
         z = apply_M(r)
         rho = z @ r
         if p is None:
+            beta = 0.0
             p = z.copy()
         else:
             num = z @ (r - r_prev) if flexible else rho
-            p = z + (num / rho_prev) * p
+            beta = num / rho_prev
+            p = z + beta * p
         q = apply_A(p)
+        if trace is not None:
+            trace.append((p.copy(), q.copy(), beta))
         alpha = rho / (p @ q)
         x = x + alpha * p
         r_prev = r

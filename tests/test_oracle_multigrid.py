@@ -301,3 +301,109 @@ def test_multigrid_iterations_nearly_mesh_independent():
 def test_unsupported_mesh_rejected():
     with pytest.raises(ValueError):
         multigrid.build_hierarchy(6, 4, np.ones((4, 6)), fem.element_stiffness(0.3), BOTTOM, 2)
+
+
+def test_rediscretised_coarse_modulus_is_the_child_mean():
+    # Sec. 2.1 rediscretisation with non-constant moduli.  (1) A field of
+    # constant strain gives every fine element the same energy density, so its
+    # Galerkin energy (P^T K P, built by the sparse product, not by assembly)
+    # is the density times the sum of the fine moduli; the rediscretised
+    # coarse element must carry the same energy, which holds for the
+    # arithmetic mean of its four children and fails for a geometric or
+    # harmonic mean or a child counted twice.  (2) A corner node of the coarse
+    # mesh touches one coarse element, so its diagonal is that element's
+    # modulus times the closed-form KE_00 = (3 - nu) / (6 (1 - nu^2)); this
+    # catches a mean assigned to the wrong coarse element.
+    nu = 0.3
+    nelx, nely = 4, 4
+    E = np.array([[1.0, 9.0, 0.5, 2.0],
+                  [4.0, 0.25, 3.0, 7.0],
+                  [0.1, 5.0, 6.0, 1.5],
+                  [8.0, 2.5, 0.75, 11.0]])
+    KE = fem.element_stiffness(nu)
+    free_edges = 0
+    red = multigrid.build_hierarchy(nelx, nely, E, KE, free_edges, 1, "rediscretize",
+                                    factor_coarsest=False)
+    gal = multigrid.build_hierarchy(nelx, nely, E, KE, free_edges, 1, "galerkin",
+                                    factor_coarsest=False)
+    J, I = np.meshgrid(np.arange(3) * 2.0, np.arange(3) * 2.0, indexing="ij")
+    for ux, uy in ((I, 0 * I), (0 * I, J), (J, I), (0.3 * I - J, 2 * J + 0.5 * I)):
+        v = np.stack([ux, uy], axis=-1).ravel()
+        e_red = v @ (red[0].K @ v)
+        e_gal = v @ (gal[0].K @ v)
+        assert e_red == pytest.approx(e_gal, rel=1e-12)
+        assert e_red > 0
+    kdiag = (3 - nu) / (6 * (1 - nu * nu))
+    diag = red[0].K.diagonal().reshape(3, 3, 2)
+    means = {(0, 0): E[0:2, 0:2].mean(), (0, 2): E[0:2, 2:4].mean(),
+             (2, 0): E[2:4, 0:2].mean(), (2, 2): E[2:4, 2:4].mean()}
+    for (j, i), m in means.items():
+        np.testing.assert_allclose(diag[j, i], [m * kdiag, m * kdiag], rtol=1e-13)
+    # The bending energy of a single coarse element differs between the two
+    # coarse operators (Galerkin resolves where the stiff children sit).
+    v = np.zeros((3, 3, 2)); v[1, 1, 0] = 1.0
+    assert abs(v.ravel() @ (red[0].K @ v.ravel()) - v.ravel() @ (gal[0].K @ v.ravel())) > 1e-3
+
+
+def _spd(n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (Q * np.geomspace(1.0, cond, n)) @ Q.T
+
+
+def test_flexible_beta_equals_fletcher_reeves_for_a_fixed_preconditioner():
+    # With a fixed symmetric positive definite M, z_{i+1} . r_i = 0 in exact
+    # arithmetic, so the flexible numerator z_{i+1} . (r_{i+1} - r_i) equals the
+    # Fletcher-Reeves one and both runs take the same steps.
+    n = 40
+    A = _spd(n, 30)
+    Minv = np.linalg.inv(_spd(n, 31, cond=20.0) + np.diag(np.diag(A)))
+    b = np.random.default_rng(32).standard_normal(n)
+    for k in range(1, 9):
+        xf, *_ = pcg.pcg(lambda v: A @ v, b, lambda r: Minv @ r, tol=0.0, max_it=k, flexible=True)
+        xr, *_ = pcg.pcg(lambda v: A @ v, b, lambda r: Minv @ r, tol=0.0, max_it=k, flexible=False)
+        assert np.linalg.norm(xf - xr) <= 1e-10 * np.linalg.norm(xr), k
+
+
+def test_flexible_beta_keeps_consecutive_directions_conjugate():
+    # With a preconditioner that changes at every call (here a new random
+    # positive diagonal each time), the flexible beta is the one that makes
+    # p_{i+1} A-orthogonal to p_i: z.(r_new - r_old) = -alpha z.A p_i and
+    # alpha = rho / p_i.A p_i give p_{i+1}.A p_i = 0.  A sign or index error
+    # in the numerator breaks the identity; the Fletcher-Reeves form, which
+    # assumes a fixed preconditioner, breaks it too (the teeth of this test).
+    n = 60
+    A = _spd(n, 33, cond=100.0)
+    b = np.random.default_rng(34).standard_normal(n)
+
+    def varying():
+        rng = np.random.default_rng(35)
+        return lambda r: rng.uniform(0.2, 5.0, r.size) * r
+
+    def worst_cosine(trace):
+        w = 0.0
+        for (p0, q0, _), (p1, _, _) in zip(trace, trace[1:]):
+            w = max(w, abs(p1 @ q0) / (np.linalg.norm(p1) * np.linalg.norm(q0)))
+        return w
+
+    tr_flex, tr_fr = [], []
+    x, it, conv, _ = pcg.pcg(lambda v: A @ v, b, varying(), tol=1e-10, max_it=1000,
+                             flexible=True, trace=tr_flex)
+    _, _, conv_fr, _ = pcg.pcg(lambda v: A @ v, b, varying(), tol=1e-10, max_it=2 * it,
+                               flexible=False, trace=tr_fr)
+    assert conv and not conv_fr
+    np.testing.assert_allclose(A @ x, b, atol=1e-8 * np.linalg.norm(b))
+    assert worst_cosine(tr_flex) < 1e-12
+    assert worst_cosine(tr_fr) > 1e-3
+    # The first step uses p_0 = z_0 (no beta).
+    assert tr_flex[0][2] == 0.0
+    # Residual replacement every 3 steps keeps the identity on the steps
+    # where r_new - r_old is the recursive update.
+    tr_rr = []
+    pcg.pcg(lambda v: A @ v, b, varying(), tol=0.0, max_it=12, flexible=True, rr_every=3,
+            trace=tr_rr)
+    for i in range(len(tr_rr) - 1):
+        if (i + 1) % 3:
+            p0, q0, _ = tr_rr[i]
+            p1 = tr_rr[i + 1][0]
+            assert abs(p1 @ q0) < 1e-12 * np.linalg.norm(p1) * np.linalg.norm(q0)

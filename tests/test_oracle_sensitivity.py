@@ -63,3 +63,51 @@ def test_bf16_rounding():
     # Just above a tie rounds up (direct rounding from float64, no float32 step).
     assert precision.round_to_bf16(1 + 2.0**-8 + 2.0**-40) == 1 + 2.0**-7
     assert precision.round_to_bf16(0.0) == 0.0
+
+
+def test_relative_element_energy_is_the_element_energy():
+    # Eq. 7: a rigid translation carries no strain, so measuring the nodal
+    # values from the element's first node changes nothing in exact
+    # arithmetic; on a field shifted by a large translation the relative form
+    # keeps its accuracy while the plain form loses digits.
+    nelx, nely = 10, 6
+    KE = fem.element_stiffness(0.3)
+    u = np.random.default_rng(3).standard_normal((nely + 1, nelx + 1, 2))
+    w_plain = sensitivity.element_energy(nelx, nely, KE, u)
+    w_rel = sensitivity.element_energy_relative(nelx, nely, KE, u)
+    np.testing.assert_allclose(w_rel, w_plain, rtol=1e-12, atol=1e-13)
+    shifted = u + np.array([3e7, -5e7])
+    w_shift = sensitivity.element_energy_relative(nelx, nely, KE, shifted)
+    np.testing.assert_allclose(w_shift, w_plain, rtol=1e-6, atol=1e-7)
+    assert np.all(w_rel >= -1e-12)  # KE is positive semi-definite
+
+
+def test_variational_energy_is_stationary_at_the_solution():
+    # Pi(u) = 2 f.u - u^T K u equals the compliance at K u = f (Eq. 6) and
+    # falls by exactly delta^T K delta away from it (checked against the
+    # assembled K, a separate code path from the element loop).
+    nelx, nely = 12, 8
+    x = dirichlet_design(nelx, nely, 4, seed=21)
+    f = load_top_edge(nelx, nely) + 0.4 * load_right_edge(nelx, nely)
+    E = fem.simp_moduli(x, EP, 3.0)
+    KE = fem.element_stiffness(0.3)
+    u = solver.solve_direct(nelx, nely, x, EP, 3.0, f)
+    pi_star = float(np.sum(sensitivity.variational_energy_terms(nelx, nely, E, KE, f, u)))
+    assert pi_star == pytest.approx(sensitivity.compliance(f, u), rel=1e-12)
+    K = fem.assemble(nelx, nely, E, KE)
+    free = fem.free_dofs(nelx, nely, fem.BOTTOM)
+    rng = np.random.default_rng(22)
+    for scale in (1e-3, 1e-1):
+        delta = np.zeros(u.size)
+        delta[free] = scale * rng.standard_normal(free.size) * np.abs(u).max()
+        ud = u + delta.reshape(u.shape)
+        pi = float(np.sum(sensitivity.variational_energy_terms(nelx, nely, E, KE, f, ud)))
+        drop = float(delta @ (K @ delta))
+        assert pi_star - pi == pytest.approx(drop, rel=1e-8)
+
+
+def test_energy_difference_sums_exactly():
+    a = np.array([1e16, 1.0, -1e16, 3.0])
+    b = np.array([2.0, 1e-20])
+    assert sensitivity.energy_difference(a, b) == 2.0 - 1e-20
+    assert sensitivity.energy_difference(a, a) == 0.0
