@@ -28,26 +28,35 @@ UNIT = "solves/s"
 EP = [1.0, 0.5, 0.25, 1e-9]
 PENAL = 3.0
 SEED = 0
-# Algorithmic work per finest-level node of the two timed kernels (see DESIGN.md):
+# Algorithmic work per finest-level node of the two timed kernels:
 #  * outer sweep p = z + beta p, q = K p, p.q in float64: 36 FP64 pipe
 #    operations (11 edge-difference add/sub, 7 core mul/fma on pre-scaled
-#    moduli, 14 edge-force add/sub, 2 fma for p, 2 fma for the dot);
+#    moduli, 14 edge-force add/sub, 2 fma for p, 2 fma for the dot); bytes:
+#    z (float32 in the mixed path: 8, float64: 16), p 16, x 16 (the lagged
+#    step x += alpha p), the element's modulus 8 in; p 16, x 16, q 16 out;
 #  * float32 fused pre-smoothing (two damped-Jacobi sweeps from zero, the
 #    first formed on the fly) carrying the CG update r -= alpha q of the last
 #    step: reads the last r and q (float64, 16 B each) and the element's bf16
 #    modulus (2 B), writes the new r (16 B), its float32 copy (8 B) and z
-#    (8 B): 66 B.
+#    (8 B): 66 B;
+#  * float64 fused pre-smoothing (float64 path): b 16, modulus 8, w/D 8 in,
+#    z 16 out: 48 B; 38 FP64 operations (K v 32, w D^-1 b 2, z + d (b - K v) 4).
 KP_OPS_PER_NODE = 36
+KP_BYTES_PER_NODE = {"mixed": 96, "fp64": 104}
 SMOOTH32_BYTES_PER_NODE = 66
-SMOOTH64_OPS_PER_NODE = 38  # K v 32, w D^-1 b 2, z + d (b - K v) 4 (first two sweeps fused)
+SMOOTH64_OPS_PER_NODE = 38
+SMOOTH64_BYTES_PER_NODE = 48
 # DRAM bytes per launch at 2048^2 from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/sweeps_2048_ncu_full.md); None once the
 # kernel changes.
 KP_TRAFFIC = 354_025_984
 SMOOTH32_TRAFFIC = 249_000_704
-# FP64 pipe: 2 operations per clock per SM (1.25 TFLOP/s nominal at 2 flops
-# per FMA), 152 SMs, 2070 MHz.
-FP64_OPS_PEAK = 2 * 152 * 2.070e9
+# Nominal float64 pipe rate, for context next to the measured one: 2
+# operations per clock per SM (1.25 TFLOP/s at 2 flops per FMA), 152 SMs,
+# 2070 MHz.
+FP64_OPS_NOMINAL = 2 * 152 * 2.070e9
+# PCG iterations of the bounded CPU sample at the full size.
+CPU_SAMPLE_ITERS = 2
 
 
 def parse():
@@ -62,7 +71,6 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sample-size", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (for profiling)")
@@ -160,33 +168,28 @@ class ClockSampler:
 # CPU oracle timing (test infrastructure; only this leg of the bench uses it)
 # ---------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
-import json, sys, time
+import json, os, sys
 sys.path.insert(0, {root!r})
 from oracle import solver
 from synth import dirichlet_design, load_top_edge
-n, nc, budget, reps, gamma = {n}, {nc}, {budget}, {reps}, {gamma}
+n, nc, max_it, gamma = {n}, {nc}, {max_it}, {gamma}
 x = dirichlet_design(n, n, 4, {seed}); f = load_top_edge(n, n)
-times, iters = [], []
-t_all = time.perf_counter()
-while True:
-    t = time.perf_counter()
-    r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol=1e-8, gamma=gamma)
-    times.append(time.perf_counter() - t); iters.append(r["iters"])
-    if (reps and len(times) >= reps) or (not reps and time.perf_counter() - t_all >= budget):
-        break
-print(json.dumps({{"times": times, "iters": iters}}))
+t = {{}}
+r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol=1e-8, max_it=max_it,
+                       gamma=gamma, timings=t)
+t.update(iters=r["iters"], converged=bool(r["converged"]), host_cores=os.cpu_count())
+print(json.dumps(t))
 """
 
 
-def oracle_sample(n, reps=0, budget=10.0, gamma=1):
-    nc = max(1, n.bit_length() - 1 - 4)  # coarsest 16 x 16, as at 2048^2 with 7 coarsenings
-    code = ORACLE_SNIPPET.format(root=ROOT, n=n, nc=nc, budget=budget, reps=reps, seed=SEED, ep=EP,
-                                 penal=PENAL, gamma=gamma)
+def oracle_run(n, nc, max_it, gamma=1):
+    """One oracle pCGMG solve (1 thread) in a subprocess, stopped after max_it
+    PCG iterations; returns its set-up, start and per-iteration wall times."""
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, nc=nc, max_it=max_it, seed=SEED, ep=EP, penal=PENAL,
+                                 gamma=gamma)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
-    d = json.loads(out.stdout.strip().splitlines()[-1])
-    d["nc"] = nc
-    return d
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def ndof(n):
@@ -209,32 +212,41 @@ def job_value(world, steps, ms_max):
     return world * steps / (ms_max / 1000.0)
 
 
-def cpu_value(d, n_sample, n_full):
-    # solves/s at the full size, scaled from the sample by the DOF ratio
-    # (pCGMG work per iteration is linear in DOFs; iteration counts are
-    # mesh-independent).
-    t = sum(d["times"]) / len(d["times"])
-    return (1.0 / t) * ndof(n_sample) / ndof(n_full)
+def cpu_sample_value(d, iters_full):
+    """solves/s of the oracle at the measured size: its set-up and start as
+    measured, plus iters_full iterations at the measured mean iteration time
+    (every PCG iteration does the same work)."""
+    t_it = sum(d["iter_s"]) / len(d["iter_s"])
+    return 1.0 / (d["setup_s"] + d["start_s"] + iters_full * t_it)
 
 
 def run_reference(args):
+    """The oracle's pCGMG on the same workload (2048^2, 7 coarsenings, tol
+    1e-8), one thread, on the host cores: ONE full solve whose PCG iterations
+    are the steps (warmup untimed, then `steps` timed, then on to
+    convergence).  value = 1 / wall time of the whole solve (set-up included)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n_full, n_s = args.size, args.sample_size
-    for _ in range(args.warmup):
-        oracle_sample(n_s, reps=1, gamma=args.gamma)
-    d = oracle_sample(n_s, reps=max(1, args.steps), gamma=args.gamma)
-    v = cpu_value(d, n_s, n_full)
-    ms = 1000.0 * sum(d["times"]) / len(d["times"])
-    sample = (f"oracle pCGMG (numpy/scipy, FP64, 1 thread) on {n_s}x{n_s} (nc={d['nc']}), "
-              f"{len(d['times'])} solves, scaled to {n_full}^2 by the DOF ratio")
+    n, nc = args.size, args.n_coarsen
+    d = oracle_run(n, nc, 1000, gamma=args.gamma)
+    its = d["iter_s"]
+    timed = its[args.warmup:args.warmup + args.steps] or its[-1:]
+    total = d["setup_s"] + d["start_s"] + sum(its)
+    v = 1.0 / total
+    sample = (f"one full oracle pCGMG solve (numpy/scipy, FP64, 1 thread of {d['host_cores']} host cores) "
+              f"at {n}x{n}, {nc} coarsenings, tol 1e-8: set-up {d['setup_s']:.1f} s + {d['iters']} "
+              f"iterations {sum(its):.1f} s; steps = PCG iterations {args.warmup}..{args.warmup + len(timed) - 1}")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"pCGMG {n_full}x{n_full} Q4 square wall (oracle sample {n_s}^2)",
-                   "iters": d["iters"], "gamma": args.gamma},
+        "steps": len(timed), "warmup": args.warmup, "ms_per_step": 1000.0 * sum(timed) / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"pCGMG {n}x{n} Q4 square wall (3 solids + void, p=3, seeded Dirichlet "
+                               f"fractions), {nc} coarsenings to 16x16, tol 1e-8; oracle, one solve",
+                   "iters": d["iters"], "converged": d["converged"], "gamma": args.gamma,
+                   "step": "one PCG iteration of the oracle solve",
+                   "ms_setup": 1000.0 * d["setup_s"], "s_total": total},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -430,15 +442,26 @@ def run_ours(args):
     gdof = ndof(n) * sum(iters) / (ms / 1000.0) / 1e9
     gdof_solve = ndof(n) * sum(iters) / (sum(solve_ms) / 1000.0) / 1e9
 
-    # Roofline of the two timed kernels (live CUDA events inside the solver graph).
+    # Roofline of the two timed kernels (live CUDA events inside the solver
+    # graph).  The float64 sweep's peak is the float64 FMA issue rate measured
+    # on this device right here (mto_measure_fp64_rate), with its clocks.
+    with ClockSampler(local) as clk_probe:
+        fp64_peak = mto.measure_fp64_rate(local)
+    fp64_probe = {"ops_per_s": fp64_peak, "nominal_ops_per_s": FP64_OPS_NOMINAL,
+                  "clocks": clk_probe.summary(),
+                  "how": "mto_measure_fp64_rate: 8 independent DFMA chains per thread, 8 x 256-thread "
+                         "blocks per SM, CUDA events, best of 5 after 3 warm-up launches"}
     kp_ms, sm_ms = kt["ms"]
     kp_ops = KP_OPS_PER_NODE * nodes / (kp_ms / 1000.0)
+    kp_gbs = KP_BYTES_PER_NODE["mixed"] * nodes / (kp_ms / 1000.0) / 1e9
     sm_bytes = SMOOTH32_BYTES_PER_NODE * nodes / (sm_ms / 1000.0)
     roofline = {"bound": "alu", "kernel": "outer sweep p=z+beta p, q=Kp, p.q (float64)",
-                "achieved": kp_ops / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "T FP64-op/s",
-                "frac": kp_ops / FP64_OPS_PEAK, "traffic": KP_TRAFFIC, "ms_per_launch": kp_ms,
+                "achieved": kp_ops / 1e12, "peak": fp64_peak / 1e12, "unit": "T FP64-op/s",
+                "frac": kp_ops / fp64_peak, "traffic": KP_TRAFFIC, "ms_per_launch": kp_ms,
                 "samples": kt["samples"][0],
-                "peak_kind": "derived: 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz"}
+                "peak_kind": "measured: float64 FMA issue rate of this GPU (fp64_peak)",
+                "hbm": {"achieved_gbs": kp_gbs, "peak_gbs": hbm_peak, "frac": kp_gbs / hbm_peak,
+                        "bytes_per_node": KP_BYTES_PER_NODE["mixed"], "peak_kind": peak_kind}}
     roofline_vcycle = {"bound": "hbm",
                        "kernel": "finest fused pre-smoothing with the CG update (float32, bf16 E; float64 r)",
                        "achieved": sm_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -487,12 +510,18 @@ def run_ours(args):
         kt64 = kernel_times(m64, 1)
         it64 = [s["iters"] for s in st64]
         v64 = job_value(world, args.fp64_steps, ms64)
+        kp64_s, sm64_s = kt64["ms"][0] / 1000.0, kt64["ms"][1] / 1000.0
         fp64 = {"solves_s": v64, "ms_per_step": ms64 / args.fp64_steps, "iters": it64,
                 "gdof_iter_s": ndof(n) * sum(it64) / (ms64 / 1000.0) / 1e9,
                 "rel_res_true": max(s["rel_res_true"] for s in st64),
                 "kernel_ms": kt64["ms"],
-                "smoother_fp64_frac_alu": SMOOTH64_OPS_PER_NODE * nodes / (kt64["ms"][1] / 1000.0) / FP64_OPS_PEAK,
-                "kp_fp64_frac_alu": KP_OPS_PER_NODE * nodes / (kt64["ms"][0] / 1000.0) / FP64_OPS_PEAK}
+                # Both bounds of the float64 sweeps: the float64 pipe (binding)
+                # and HBM (the >= 60% target, out of reach while the pipe binds).
+                "kp_fp64_frac_alu": KP_OPS_PER_NODE * nodes / kp64_s / fp64_peak,
+                "kp_fp64_frac_hbm": KP_BYTES_PER_NODE["fp64"] * nodes / kp64_s / 1e9 / hbm_peak,
+                "smoother_fp64_frac_alu": SMOOTH64_OPS_PER_NODE * nodes / sm64_s / fp64_peak,
+                "smoother_fp64_frac_hbm": SMOOTH64_BYTES_PER_NODE * nodes / sm64_s / 1e9 / hbm_peak,
+                "clocks": clk64}
         m64.close()
 
     batched = None
@@ -504,11 +533,18 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        d = oracle_sample(args.sample_size, budget=10.0, gamma=args.gamma)
-        cpu = {"value": cpu_value(d, args.sample_size, n), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"oracle pCGMG (numpy/scipy FP64, 1 thread) on {args.sample_size}^2, "
-                          f"{len(d['times'])} solves ({sum(d['times']):.1f} s), iters {d['iters'][0]}, "
-                          f"scaled to {n}^2 by the DOF ratio")}
+        # A bounded sample of the same workload: the oracle's set-up and its
+        # first CPU_SAMPLE_ITERS PCG iterations at the full size, measured;
+        # the solve is completed at the measured iteration time with the
+        # iteration count of the float64 GPU path on the same input (the
+        # oracle's count is within one of it, as the parity tests check).
+        d = oracle_run(n, nc, CPU_SAMPLE_ITERS, gamma=args.gamma)
+        iters_full = fp64["iters"][0] if fp64 else iters[0]
+        cpu = {"value": cpu_sample_value(d, iters_full), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"oracle pCGMG (numpy/scipy FP64, 1 thread of {d['host_cores']} host cores) at "
+                          f"{n}^2, measured: set-up {d['setup_s']:.1f} s + start {d['start_s']:.2f} s + "
+                          f"{len(d['iter_s'])} PCG iterations at {sum(d['iter_s']) / len(d['iter_s']):.2f} s; "
+                          f"completed to {iters_full} iterations (the float64 GPU path's count)")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -525,7 +561,7 @@ def run_ours(args):
         "rel_res_true_max": max(s["rel_res_true"] for s in stats),
         "ms_setup": stats[-1]["ms_setup"], "ms_solve": solve_ms,
         "fp64": fp64, "speedup_mixed_vs_fp64": (value / fp64["solves_s"]) if fp64 else None,
-        "roofline": roofline, "roofline_vcycle": roofline_vcycle,
+        "roofline": roofline, "roofline_vcycle": roofline_vcycle, "fp64_peak": fp64_probe,
         "launch_shapes": shapes_mixed, "batched": batched, "mesh_sweep": sweep,
         "clocks": clocks, "gpu_launches": nlaunch, "e2e": e2e, "cpu_baseline": cpu,
     }

@@ -250,6 +250,14 @@ mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu, int n_phas
  * launched (each graph launch counts its kernel nodes).  Timing adds event
  * nodes to the graph; leave it off outside measurements. */
 mto_status mto_set_kernel_timing(mto_ctx* ctx, int enable);
+/* Measured issue rate of the float64 pipe on `device`: a kernel in which every
+ * thread runs eight independent chains of dependent float64 fused
+ * multiply-adds, eight 256-thread blocks per SM, timed with CUDA events on
+ * cuda_stream (3 warm-up launches, best of 5; synchronises).  *ops_per_s =
+ * FMA instructions per second, the unit in which the float64 sweeps' work is
+ * counted (one add, multiply or FMA = one operation).  The paper has no
+ * counterpart: it is the denominator of the float64 kernels' roofline. */
+mto_status mto_measure_fp64_rate(int device, void* cuda_stream, double* ops_per_s);
 mto_status mto_get_kernel_times(mto_ctx* ctx, double* ms_avg, long long* samples);
 mto_status mto_get_launch_count(mto_ctx* ctx, long long* launches);
 

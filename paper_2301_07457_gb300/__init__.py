@@ -26,7 +26,8 @@ from ._lib import (  # noqa: F401
     SolveStats,
 )
 
-__all__ = ["Mesh", "Batch", "Compliance", "compliance", "MtoError", "SolverOpts", "SolveStats"]
+__all__ = ["Mesh", "Batch", "Compliance", "compliance", "measure_fp64_rate", "MtoError", "SolverOpts",
+           "SolveStats"]
 
 
 def _ptr(t):
@@ -43,6 +44,17 @@ def _dev_f64(t, device, name):
     if t.device != device or t.dtype != torch.float64:
         raise ValueError(f"{name} must be a float64 tensor on {device}")
     return t.contiguous()
+
+
+def measure_fp64_rate(device=None):
+    """Measured float64 FMA issue rate of the device (operations per second)."""
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    v = ctypes.c_double()
+    with torch.cuda.device(dev):
+        _lib.check(lib.mto_measure_fp64_rate(dev.index, _stream(dev), ctypes.byref(v)),
+                   "mto_measure_fp64_rate")
+    return v.value
 
 
 class Mesh:
@@ -79,6 +91,10 @@ class Mesh:
         self.n_phase = None
         self.E_phase = None
         self.penal = None
+        # Counts set_design calls: a saved value tells whether the operators
+        # on the device are still those of a given design.
+        self.design_version = 0
+        self.last_solve_stats = None
 
     # -- lifecycle -----------------------------------------------------------
     def close(self):
@@ -113,6 +129,7 @@ class Mesh:
         _lib.check(code, "mto_set_design")
         self.n_phase, self.E_phase, self.penal = x.shape[0], list(E_phase), float(penal)
         self._x = x
+        self.design_version += 1
 
     def solve(self, f, u0=None, raise_on_failure=True):
         """Solve K u = f (f: [n_rhs?][nely+1][nelx+1][2] float64).  Returns (u, stats)."""
@@ -130,6 +147,7 @@ class Mesh:
             _lib.check(code, "mto_solve")
         d = st.as_dict()
         d["status"] = _lib.STATUS[code]
+        self.last_solve_stats = d
         return u, d
 
     def compliance_grad(self, f, u, want_grad=True):
@@ -294,8 +312,11 @@ class Compliance(torch.autograd.Function):
 
     The compliance problem is self-adjoint (Eq. 6), so the backward needs no
     second solve: dC/dx_{e,i} = -p x^{p-1} E_i u_e^T KE u_e with the forward u.
-    When keep_u is False the forward does not hold u; the backward re-solves
-    for it (warm-started from zero), trading time for memory.
+    The backward rebuilds the operators only if the mesh was given another
+    design since the forward (mesh.design_version).  When keep_u is False the
+    forward keeps only a float32 copy of u (half the memory of the float64
+    solution); the backward re-solves for u warm-started from it, which takes
+    fewer PCG iterations than a cold solve.
     """
 
     @staticmethod
@@ -304,16 +325,19 @@ class Compliance(torch.autograd.Function):
         u, _ = mesh.solve(f)
         C, _ = mesh.compliance_grad(f, u, want_grad=False)
         ctx.mesh, ctx.E_phase, ctx.penal, ctx.keep_u = mesh, E_phase, penal, keep_u
-        ctx.save_for_backward(x.detach(), f, u if keep_u else torch.empty(0, device=f.device))
+        ctx.design_version = mesh.design_version
+        ctx.save_for_backward(x.detach(), f, u if keep_u else u.float())
         return C.sum()
 
     @staticmethod
     def backward(ctx, gC):
         x, f, u = ctx.saved_tensors
         mesh = ctx.mesh
-        mesh.set_design(x, ctx.E_phase, ctx.penal)
+        if mesh.design_version != ctx.design_version:
+            mesh.set_design(x, ctx.E_phase, ctx.penal)
+            ctx.design_version = mesh.design_version
         if not ctx.keep_u:
-            u, _ = mesh.solve(f)
+            u, _ = mesh.solve(f, u0=u.double())
         _, g = mesh.compliance_grad(f, u, want_grad=True)
         return g * gC, None, None, None, None, None
 

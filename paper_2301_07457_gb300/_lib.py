@@ -114,6 +114,7 @@ SIGNATURES = {
     "mto_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "mto_get_kernel_times": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "mto_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int, _P, _D]),
     "mto_destroy": (None, [_P]),
     "mto_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mto_cuda_error_string": (ctypes.c_char_p, []),

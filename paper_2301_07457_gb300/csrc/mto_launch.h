@@ -121,6 +121,12 @@ cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, cons
 // Opt-in shared memory of the GEMV for n free coarsest DOFs (b is staged in
 // shared memory: 8 n bytes), once per size, outside any stream capture.
 cudaError_t prepare_coarsest_gemv(int n);
+// Raises the opt-in dynamic shared memory limit of `func` on the current
+// device to at least `bytes` (no call at 48 KiB or less).  The limit belongs
+// to the kernel for the whole process, so it only ever grows: a context that
+// needs less never lowers the limit another live context relies on.
+// Thread-safe (one mutex for all kernels and devices).
+cudaError_t raise_max_dynamic_smem(const void* func, size_t bytes);
 
 // PCG scalars of a fresh solve; loop condition of the device-side solver loop;
 // per-solve outcome record.

@@ -11,8 +11,7 @@
 // loading the library holds until the process exits.
 #include <mutex>
 
-#include "mto.h"
-#include "mto_launch.h"
+#include "mto_ctx.cuh"
 
 using namespace mto;
 
@@ -83,26 +82,35 @@ extern "C" mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu,
       !(penal >= 1.0 && penal <= 64.0) || !f_dev || !u_dev || !compliance_dev ||
       (dcdx_dev && !x_dev))
     return MTO_ERR_ARG;
-  const long long nodes = (long long)(nelx + 1) * (nely + 1);
+  const long long nodes = ((long long)nelx + 1) * ((long long)nely + 1);
   if (nodes > NA_MAX_NODES) return MTO_ERR_UNSUPPORTED_MESH;
   for (int i = 0; i < n_phase; ++i)
     if (!(E_phase[i] > 0.0 && E_phase[i] < 1e300)) return MTO_ERR_ARG;
-  double* scratch = nullptr;
-  if (scratch_for(device, &scratch) != cudaSuccess) return MTO_ERR_CUDA;
-  int prev = 0;
-  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess)
+  // Every MTO_ERR_CUDA below records its cause for mto_cuda_error_string.
+  auto fail = [](cudaError_t e) {
+    g_last_cuda = e;
     return MTO_ERR_CUDA;
+  };
+  double* scratch = nullptr;
+  cudaError_t e = scratch_for(device, &scratch);
+  if (e != cudaSuccess) return fail(e);
+  int prev = 0;
+  e = cudaGetDevice(&prev);
+  if (e == cudaSuccess) e = cudaSetDevice(device);
+  if (e != cudaSuccess) return fail(e);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   mto_status st = MTO_OK;
   // The ticket must start at zero; the partials are always written before use.
-  if (cudaMemsetAsync(scratch + 2 * NA_MAX_BLOCKS, 0, sizeof(unsigned), s) != cudaSuccess) {
-    st = MTO_ERR_CUDA;
+  e = cudaMemsetAsync(scratch + 2 * NA_MAX_BLOCKS, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) {
+    st = fail(e);
   } else {
     const int blocks = (int)((nodes + NA_NODES_PER_BLOCK - 1) / NA_NODES_PER_BLOCK);
     dot_noalloc_kernel<<<blocks, NA_NT, 0, s>>>(nodes, reinterpret_cast<const double2*>(f_dev),
                                                 reinterpret_cast<const double2*>(u_dev), scratch,
                                                 compliance_dev);
-    if (cudaGetLastError() != cudaSuccess) st = MTO_ERR_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) st = fail(e);
   }
   if (st == MTO_OK && dcdx_dev) {
     PhaseTable ph{};
@@ -112,9 +120,8 @@ extern "C" mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu,
     const FineConst<double> kf = {kap, kap * nu, kap * (1.0 + gs) / 3.0, kap * gs};
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (launch_sensitivity(nelx, nely, n_phase, x_dev, ph, penal, ipenal, kf, u_dev, dcdx_dev, 0, s,
-                           sms) != cudaSuccess)
-      st = MTO_ERR_CUDA;
+    e = launch_sensitivity(nelx, nely, n_phase, x_dev, ph, penal, ipenal, kf, u_dev, dcdx_dev, 0, s, sms);
+    if (e != cudaSuccess) st = fail(e);
   }
   cudaSetDevice(prev);
   return st;

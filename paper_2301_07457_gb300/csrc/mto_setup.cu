@@ -675,20 +675,16 @@ static CholPlan chol_plan(int n, int bw) {
 }
 
 template <bool LSMEM, int NS> static cudaError_t set_axpy_smem(size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(inverse_axpy_kernel<LSMEM, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  return raise_max_dynamic_smem((const void*)inverse_axpy_kernel<LSMEM, NS>, bytes);
 }
 
 cudaError_t prepare_cholesky_inverse(int n, int bw) {
   const CholPlan pl = chol_plan(n, bw);
   cudaError_t e = cudaSuccess;
   if (pl.band_smem)
-    e = cudaFuncSetAttribute(cholesky_band_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(pl.band + pl.pairs));
-  else if (pl.pairs > 48 * 1024)
-    e = cudaFuncSetAttribute(cholesky_band_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pl.pairs);
+    e = raise_max_dynamic_smem((const void*)cholesky_band_kernel<true>, pl.band + pl.pairs);
+  else
+    e = raise_max_dynamic_smem((const void*)cholesky_band_kernel<false>, pl.pairs);
   if (e != cudaSuccess) return e;
   if (pl.slots == 2) {
     return pl.axpy_smem ? set_axpy_smem<true, 2>(pl.band + pl.ybuf) : set_axpy_smem<false, 2>(pl.ybuf);
@@ -697,11 +693,9 @@ cudaError_t prepare_cholesky_inverse(int n, int bw) {
     return pl.axpy_smem ? set_axpy_smem<true, 4>(pl.band + pl.ybuf) : set_axpy_smem<false, 4>(pl.ybuf);
   }
   if (pl.inv_smem)
-    e = cudaFuncSetAttribute(inverse_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(pl.band + pl.win));
-  else if (pl.win > 48 * 1024)
-    e = cudaFuncSetAttribute(inverse_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pl.win);
+    e = raise_max_dynamic_smem((const void*)inverse_cols_kernel<true>, pl.band + pl.win);
+  else
+    e = raise_max_dynamic_smem((const void*)inverse_cols_kernel<false>, pl.win);
   return e;
 }
 

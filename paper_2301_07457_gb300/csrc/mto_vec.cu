@@ -1,6 +1,10 @@
 // Pointwise kernels of the PCG recurrence (Alg. 2), the first smoothing sweep
 // from a zero iterate (Sec. 2.3 with x_0 = 0), layout conversions and the
 // coarsest-grid solve of Alg. 1 (l = 0) as a dense product with K_0^-1.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "mto_gemv.cuh"
 #include "mto_launch.h"
 
@@ -361,15 +365,27 @@ cudaError_t launch_coarsest_gemv(const Grid& g, int n, const int* free_idx, cons
                     reinterpret_cast<const T*>(b), reinterpret_cast<T*>(z),
                     static_cast<const DevScalars*>(sc));
 }
+cudaError_t raise_max_dynamic_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> current;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = current[{dev, func}];
+  if (bytes <= have) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 cudaError_t prepare_coarsest_gemv(int n) {
   if (n > GEMV_MAXN) return cudaErrorInvalidValue;
-  const int bytes = n * (int)sizeof(double);
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(coarsest_gemv_kernel<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const size_t bytes = (size_t)n * sizeof(double);
+  cudaError_t e = raise_max_dynamic_smem((const void*)coarsest_gemv_kernel<double>, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(coarsest_gemv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes);
+  return raise_max_dynamic_smem((const void*)coarsest_gemv_kernel<float>, bytes);
 }
 
 template cudaError_t launch_coarsest_gemv<double>(const Grid&, int, const int*, const double*,

@@ -61,9 +61,16 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("RANK", "1")
 
     class Args:
-        size, sample_size, warmup, steps, gpus = 2048, 512, 3, 5, 2
+        size, n_coarsen, warmup, steps, gpus, gamma = 2048, 7, 3, 5, 2, 1
 
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1))
+    monkeypatch.setattr(bench, "oracle_run", lambda *a, **k: called.append(1))
     assert bench.run_reference(Args()) == 0
     assert not called
+
+
+def test_cpu_sample_completes_the_solve_at_the_measured_iteration_time():
+    sys.path.insert(0, ROOT)
+    import bench
+    d = {"setup_s": 20.0, "start_s": 0.5, "iter_s": [2.0, 2.2]}
+    assert bench.cpu_sample_value(d, 32) == 1.0 / (20.0 + 0.5 + 32 * 2.1)

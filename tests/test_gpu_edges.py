@@ -179,3 +179,28 @@ def test_large_coarsest_system(mto, nelx, nely, n0):
     u, st = mm.solve(to_dev(f))
     assert solver.true_relative_residual(nelx, nely, E, f, u.cpu().numpy()) <= 1e-8
     mm.close()
+
+
+def test_two_live_contexts_with_large_coarsest_systems(mto):
+    # The opt-in shared memory of the coarsest factorisation and GEMV kernels
+    # is a per-process attribute of each kernel.  Creating a context with a
+    # smaller coarsest system (8,320 DOFs, 66.5 KB) after one with a larger
+    # system (16,640 DOFs, 133 KB) must not lower the limit the larger one
+    # launches with: its set_design and solve still work.
+    nelx, nely = 128, 256
+    x = dirichlet_design(nelx, nely, 4, seed=77)
+    f = load_top_edge(nelx, nely)
+    big = mto.Mesh(nelx, nely, n_coarsen=1, tol=1e-10)
+    small = mto.Mesh(128, 128, n_coarsen=1, tol=1e-10)
+    assert big.info()["coarsest_free_dofs"] == 16640
+    assert small.info()["coarsest_free_dofs"] == 8320
+    big.set_design(to_dev(x), EP, 3.0)
+    u, st = big.solve(to_dev(f))
+    assert st["converged"] == 1
+    assert rel(u.cpu().numpy(), solver.solve_direct(nelx, nely, x, EP, 3.0, f)) < 1e-7
+    xs = dirichlet_design(128, 128, 4, seed=78)
+    small.set_design(to_dev(xs), EP, 3.0)
+    us, sts = small.solve(to_dev(load_top_edge(128, 128)))
+    assert sts["converged"] == 1
+    small.close()
+    big.close()

@@ -175,3 +175,31 @@ def test_multiple_rhs_and_warm_start(mto):
     for k in range(2):
         assert abs(C[k].item() - float(np.dot(F[k].ravel(), U[k].cpu().numpy().ravel()))) < 1e-12 * abs(C[k].item())
     mesh.close()
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-10])
+def test_mixed_pcg_matches_oracle_reading(mto, tol):
+    # The mixed path's PCG against the oracle's reading of it: the outer CG in
+    # float64 with flexible beta and residual replacement every 25 steps,
+    # preconditioned by a V-cycle built from the bfloat16-rounded moduli (the
+    # oracle's V-cycle runs in float64, the GPU's in float32, so the iteration
+    # counts may differ by a step or two).  u is compared element by element
+    # with the oracle's iterate and with the direct solve.
+    nelx = nely = 256
+    x = dirichlet_design(nelx, nely, 4, seed=0)
+    f = load_top_edge(nelx, nely)
+    E = fem.simp_moduli(x, EP, 3.0)
+    ref = solver.solve_pcgmg(nelx, nely, x, EP, 3.0, f, n_coarsen=4, tol=tol,
+                             vcycle_E=precision.round_to_bf16(E), flexible=True, rr_every=25)
+    ud = solver.solve_direct(nelx, nely, x, EP, 3.0, f)
+    mesh = mto.Mesh(nelx, nely, n_coarsen=4, tol=tol, precision="mixed", rr_every=25, flexible=True,
+                    max_it=200)
+    mesh.set_design(to_dev(x), EP, 3.0)
+    u, st = mesh.solve(to_dev(f))
+    un = u.cpu().numpy()
+    assert st["converged"] == 1, st
+    assert abs(st["iters"] - ref["iters"]) <= 2, (st["iters"], ref["iters"])
+    assert rel(un, ref["u"]) <= 1e-6
+    assert rel(un, ud) <= 100 * tol
+    assert solver.true_relative_residual(nelx, nely, E, f, un) <= tol
+    mesh.close()

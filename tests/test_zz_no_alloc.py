@@ -70,3 +70,7 @@ def test_noalloc_rejects_oversized_mesh():
     assert code == _lib.ERR_UNSUPPORTED_MESH
     code = lib.mto_compliance_grad_noalloc(8, 8, 0.3, 4, p, Ep, 3.0, None, p, p, None, 0, None)
     assert code == _lib.ERR_ARG
+    # The node count is formed in 64 bits: INT_MAX columns do not wrap around
+    # to a small count that would pass the size check.
+    code = lib.mto_compliance_grad_noalloc(2**31 - 1, 1, 0.3, 4, p, Ep, 3.0, p, p, p, None, 0, None)
+    assert code == _lib.ERR_UNSUPPORTED_MESH
