@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-poisson", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (for profiling)")
     ap.add_argument("--sweep-outer", type=int, default=50)
     ap.add_argument("--study", choices=["levels"], default=None,
@@ -320,6 +321,49 @@ def run_batched(mto, dev, local):
     return out
 
 
+# Table 1 (Sec. 5.1): the paper's pCGMG wall times for the Poisson problem,
+# hardware and language not stated (context only; the 32 x 32 entry is
+# printed without a unit).
+TABLE1_PCGMG_S = {16: 0.23, 32: 2.62, 64: 0.56, 128: 0.65, 256: 0.41}
+
+
+def run_poisson(mto, dev, local, reps=20):
+    """Scalar Poisson pCGMG of Sec. 5.1 on Table 1's meshes (16^2 ... 256^2,
+    coarsened to 2 x 2), f = 1 at every node, tol 1e-8: one cluster kernel
+    per solve; device time per solve (median of reps), and the throughput of
+    64 right-hand sides at 256^2 solved by concurrent clusters in one launch."""
+    import torch
+    out = {}
+    for n in sorted(TABLE1_PCGMG_S):
+        nc = n.bit_length() - 2
+        p = mto.Poisson(n, n, n_coarsen=nc, tol=1e-8, device=local)
+        f = torch.ones((n + 1, n + 1), dtype=torch.float64, device=dev)
+        p.solve(f)
+        ms = []
+        for _ in range(reps):
+            _, st = p.solve(f)
+            ms.append(st["ms_solve"])
+        ms.sort()
+        t = ms[len(ms) // 2]
+        out[str(n)] = {"n_coarsen": nc, "cluster_ctas": p.info()["cluster_ctas"], "iters": st["iters"],
+                       "ms_solve": t, "rel_res_true": st["rel_res_true"],
+                       "gdof_iter_s": (n + 1) ** 2 * st["iters"] / (t / 1000.0) / 1e9,
+                       "paper_pcgmg_s": TABLE1_PCGMG_S[n]}
+        p.close()
+    n = 256
+    p = mto.Poisson(n, n, n_coarsen=n.bit_length() - 2, tol=1e-8, device=local)
+    F = torch.ones((64, n + 1, n + 1), dtype=torch.float64, device=dev)
+    p.solve(F)
+    ms = []
+    for _ in range(5):
+        _, st = p.solve(F)
+        ms.append(st["ms_solve"])
+    t = min(ms)
+    out["batch_256_64rhs"] = {"ms": t, "solves_s": 64 / (t / 1000.0), "iters_total": st["iters"]}
+    p.close()
+    return out
+
+
 def run_sweep(mto, dev, local, n_outer):
     """Mesh sweep: the alternating active-phase loop (float64 solves, each
     warm-started from the previous u) at 256^2, 512^2, 1024^2 with 4, 5, 6
@@ -527,6 +571,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = run_batched(mto, dev, local)
+    poisson_t1 = None
+    if not args.no_poisson:
+        poisson_t1 = run_poisson(mto, dev, local)
     sweep = None
     if not args.no_sweep:
         sweep = run_sweep(mto, dev, local, args.sweep_outer)
@@ -563,6 +610,7 @@ def run_ours(args):
         "fp64": fp64, "speedup_mixed_vs_fp64": (value / fp64["solves_s"]) if fp64 else None,
         "roofline": roofline, "roofline_vcycle": roofline_vcycle, "fp64_peak": fp64_probe,
         "launch_shapes": shapes_mixed, "batched": batched, "mesh_sweep": sweep,
+        "poisson_table1": poisson_t1,
         "clocks": clocks, "gpu_launches": nlaunch, "e2e": e2e, "cpu_baseline": cpu,
     }
     mixed.close()

@@ -239,6 +239,69 @@ mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu, int n_phas
                                        double* compliance_dev, double* dcdx_dev, int device,
                                        void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Scalar Poisson problem (Sec. 5.1, Table 1): -Laplace(u) = f on an
+ * nelx x nely mesh of unit bilinear (Q4) elements, u = 0 on all four edges,
+ * solved by the same pCGMG (Alg. 2 preconditioned by one V-cycle of Alg. 1,
+ * damped Jacobi, bilinear transfers R = P^T, coarsest grid by a dense
+ * inverse factored with Alg. 3).  One DOF per node; nodal vectors are
+ * [nely+1][nelx+1] float64.  The constant-coefficient Q4 Laplacian is the
+ * 9-point stencil (8 u_n - sum of the 8 neighbours) / 3 on every grid (its
+ * Galerkin coarse operator is the same stencil).  Float64 throughout.
+ *
+ * A solve is ONE kernel launch: each right-hand side is solved by one
+ * thread-block cluster (cluster_ctas CTAs; 0 = chosen by mesh size, one CTA
+ * up to 4,096 interior nodes, at most 16) that runs the whole PCG loop with
+ * hardware cluster barriers; right-hand sides run as concurrent clusters.
+ * --------------------------------------------------------------------------- */
+typedef struct mto_poisson mto_poisson;
+typedef struct {
+  double tol;        /* stop when ||r||_2 <= tol ||f||_2 over the interior nodes */
+  int max_it;        /* maximum PCG iterations */
+  double omega;      /* damped-Jacobi weight, 0 < omega <= 1 */
+  int nu1, nu2;      /* pre- and post-smoothing sweeps, 1..16 */
+  int n_coarsen;     /* coarsenings (Sec. 5.1 coarsens down to a 2 x 2 grid) */
+  int cluster_ctas;  /* 0 (automatic), 1, 2, 4, 8 or 16 CTAs per right-hand side; more than
+                        one only when the finest grid has over 4,096 interior nodes, and at
+                        most what the device can schedule */
+} mto_poisson_opts;
+
+/* Defaults: tol 1e-8, max_it 500, omega 0.6, nu1 = nu2 = 2, n_coarsen 3,
+ * cluster_ctas 0. */
+void mto_poisson_default_opts(mto_poisson_opts* opts);
+
+/* Creates the solver for an nelx x nely mesh (both >= 2, divisible by
+ * 2^n_coarsen; the coarsest grid needs at least one and at most 1,024
+ * interior nodes, else MTO_ERR_UNSUPPORTED_MESH) and factors the coarsest
+ * grid's matrix on the device (Alg. 3, band Cholesky, then K_0^-1).  device:
+ * CUDA ordinal; cuda_stream: the caller's stream (work is ordered after it
+ * on entry to every call and before it on return). */
+mto_status mto_poisson_create(mto_poisson** out, int nelx, int nely, const mto_poisson_opts* opts,
+                              int device, void* cuda_stream);
+
+/* Solves K u = f for n_rhs (1..64) right-hand sides at once.
+ * f_dev: device float64 [n_rhs][nely+1][nelx+1] (boundary values ignored).
+ * u_dev: device, same layout: in, the warm start (zeros = cold start; its
+ * boundary values are ignored); out, the solution, zero on the boundary.
+ * stats: host, may be NULL (iterations summed over the right-hand sides,
+ * residuals of the last one).  Synchronises.  Returns MTO_ERR_NOT_CONVERGED
+ * or MTO_ERR_BREAKDOWN when a right-hand side failed (its u holds the last
+ * iterate). */
+mto_status mto_poisson_solve(mto_poisson* p, int n_rhs, const double* f_dev, double* u_dev,
+                             mto_solve_stats* stats);
+
+/* Diagnostics (enqueue only).  y = K v on the finest grid with v read as
+ * zero on the boundary, y zero there; z = one V-cycle (Alg. 1 from U = 0)
+ * applied to r.  Vectors: device float64 [nely+1][nelx+1]. */
+mto_status mto_poisson_apply_operator(mto_poisson* p, const double* v_dev, double* y_dev);
+mto_status mto_poisson_apply_preconditioner(mto_poisson* p, const double* r_dev, double* z_dev);
+
+/* Number of grids, interior nodes of the coarsest grid, CTAs per cluster
+ * in use, and kernels launched so far (any may be NULL). */
+mto_status mto_poisson_get_info(mto_poisson* p, int* n_levels, int* coarsest_free, int* cluster_ctas,
+                                long long* launches);
+void mto_poisson_destroy(mto_poisson* p);
+
 /* Measurement hooks.
  * mto_set_kernel_timing(ctx, 1) records CUDA events (on the context's stream,
  * inside the solver's CUDA graph) around two hot kernels of every PCG

@@ -26,8 +26,8 @@ from ._lib import (  # noqa: F401
     SolveStats,
 )
 
-__all__ = ["Mesh", "Batch", "Compliance", "compliance", "measure_fp64_rate", "MtoError", "SolverOpts",
-           "SolveStats"]
+__all__ = ["Mesh", "Batch", "Poisson", "Compliance", "compliance", "measure_fp64_rate", "MtoError",
+           "SolverOpts", "SolveStats"]
 
 
 def _ptr(t):
@@ -305,6 +305,84 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Poisson:
+    """The scalar Poisson problem of Sec. 5.1 (-Laplace u = f, u = 0 on the
+    boundary, nelx x nely unit Q4 elements) solved by pCGMG in one cluster
+    kernel launch per solve.  Nodal vectors are float64 [ny+1][nx+1] (or
+    [n_rhs][ny+1][nx+1]) on the device."""
+
+    def __init__(self, nelx, nely, n_coarsen=3, tol=1e-8, max_it=500, omega=0.6, nu1=2, nu2=2,
+                 cluster_ctas=0, device=None):
+        lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        o = _lib.PoissonOpts()
+        lib.mto_poisson_default_opts(ctypes.byref(o))
+        o.tol, o.max_it, o.omega, o.nu1, o.nu2 = tol, max_it, omega, nu1, nu2
+        o.n_coarsen, o.cluster_ctas = n_coarsen, cluster_ctas
+        self.opts, self.nelx, self.nely, self._lib = o, nelx, nely, lib
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = lib.mto_poisson_create(ctypes.byref(self._h), nelx, nely, ctypes.byref(o),
+                                          self.device.index, _stream(self.device))
+        _lib.check(code, "mto_poisson_create")
+
+    @property
+    def node_shape(self):
+        return (self.nely + 1, self.nelx + 1)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.mto_poisson_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        nl, n0, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        la = ctypes.c_longlong()
+        _lib.check(self._lib.mto_poisson_get_info(self._h, ctypes.byref(nl), ctypes.byref(n0), ctypes.byref(c),
+                                                  ctypes.byref(la)), "mto_poisson_get_info")
+        return {"n_levels": nl.value, "coarsest_free_dofs": n0.value, "cluster_ctas": c.value,
+                "launches": la.value}
+
+    def solve(self, f, u0=None, raise_on_failure=True):
+        """Solve K u = f (f: [n_rhs?][nely+1][nelx+1] float64).  Returns (u, stats)."""
+        f = _dev_f64(f, self.device, "f")
+        if f.shape[-2:] != self.node_shape:
+            raise ValueError(f"f must end in {self.node_shape}")
+        u = torch.zeros_like(f) if u0 is None else _dev_f64(u0, self.device, "u0").clone()
+        n_rhs = f.shape[0] if f.dim() == 3 else 1
+        st = SolveStats()
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_poisson_solve(self._h, n_rhs, _ptr(f), _ptr(u), ctypes.byref(st))
+        if code not in (_lib.OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_BREAKDOWN) or (
+                raise_on_failure and code != _lib.OK):
+            _lib.check(code, "mto_poisson_solve")
+        d = st.as_dict()
+        d["status"] = _lib.STATUS[code]
+        return u, d
+
+    def apply_operator(self, v):
+        v = _dev_f64(v, self.device, "v")
+        y = torch.empty_like(v)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.mto_poisson_apply_operator(self._h, _ptr(v), _ptr(y)),
+                       "mto_poisson_apply_operator")
+        return y
+
+    def apply_preconditioner(self, r):
+        r = _dev_f64(r, self.device, "r")
+        z = torch.empty_like(r)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.mto_poisson_apply_preconditioner(self._h, _ptr(r), _ptr(z)),
+                       "mto_poisson_apply_preconditioner")
+        return z
 
 
 class Compliance(torch.autograd.Function):

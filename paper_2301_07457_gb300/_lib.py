@@ -61,6 +61,18 @@ class SolveStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PoissonOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("max_it", ctypes.c_int),
+        ("omega", ctypes.c_double),
+        ("nu1", ctypes.c_int),
+        ("nu2", ctypes.c_int),
+        ("n_coarsen", ctypes.c_int),
+        ("cluster_ctas", ctypes.c_int),
+    ]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [
         ("n_phase", ctypes.c_int),
@@ -115,6 +127,15 @@ SIGNATURES = {
     "mto_get_kernel_times": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int, _P, _D]),
+    "mto_poisson_default_opts": (None, [ctypes.POINTER(PoissonOpts)]),
+    "mto_poisson_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(PoissonOpts), ctypes.c_int, _P]),
+    "mto_poisson_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(SolveStats)]),
+    "mto_poisson_apply_operator": (ctypes.c_int, [_P, _P, _P]),
+    "mto_poisson_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
+    "mto_poisson_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+    "mto_poisson_destroy": (None, [_P]),
     "mto_destroy": (None, [_P]),
     "mto_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mto_cuda_error_string": (ctypes.c_char_p, []),

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmto.so")
 SOURCES = ["mto_api.cu", "mto_sweep64.cu", "mto_sweep32.cu", "mto_setup.cu", "mto_vec.cu",
-           "mto_noalloc.cu", "mto_batch.cu", "mto_probe.cu"]
+           "mto_noalloc.cu", "mto_batch.cu", "mto_probe.cu", "mto_poisson.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

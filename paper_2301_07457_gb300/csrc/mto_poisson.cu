@@ -1,0 +1,939 @@
+// Scalar Poisson pCGMG (Sec. 5.1): -Laplace(u) = f on an nelx x nely mesh of
+// unit Q4 elements, u = 0 on the four edges, solved by PCG (Alg. 2)
+// preconditioned by one V-cycle (Alg. 1) with damped-Jacobi smoothing
+// (Sec. 2.3), bilinear transfers and a dense inverse on the coarsest grid
+// (factored by Alg. 3).
+//
+// The assembled constant-coefficient Q4 Laplacian is the 9-point stencil
+// (K u)(n) = (8 u_n - sum of the 8 neighbours) / 3, its diagonal 8/3.  The
+// Galerkin coarse operator P^T K P with bilinear P is the same stencil on
+// every grid (the 2-D element matrix does not depend on the element size),
+// so no coarse operator is stored.
+//
+// Execution: the whole solve is ONE kernel launch.  Each right-hand side is
+// solved by one thread-block cluster of C CTAs (C = 1 for small meshes, up to
+// 16): the CTAs own blocks of node rows of every large level and separate
+// dependent phases with the hardware cluster barrier; scalar reductions are
+// all-gathered through distributed shared memory and summed in rank order,
+// so every CTA holds the same scalars and takes the same branches.  Levels
+// with at most LOCAL_MAX_NODES interior nodes (and the coarsest solve) run
+// inside CTA 0 alone with block barriers.  All vectors live in global memory
+// (a few MB: L2-resident).  There is no spin-wait: every barrier is a
+// hardware barrier of the block or the cluster.
+#include <cooperative_groups.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mto_ctx.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int PNT = 512;                // threads per CTA
+constexpr int PWARPS = PNT / 32;
+constexpr int PMAXC = 16;               // CTAs per cluster (non-portable above 8)
+constexpr int PMAXL = 16;               // grids
+constexpr int LOCAL_MAX_NODES = 4096;   // interior nodes of a level run by CTA 0 alone
+constexpr int PMAX_COARSE = 1024;       // interior nodes of the coarsest grid (dense inverse)
+constexpr int PMAX_RHS = 64;
+
+enum { PMODE_SOLVE = 0, PMODE_PRECOND = 1, PMODE_APPLY = 2 };
+enum { PST_RUNNING = 0, PST_CONVERGED = 1, PST_MAXIT = 2, PST_BREAKDOWN = 3 };
+
+struct PLevel {
+  int nx, ny;       // elements; nodes (nx + 1) x (ny + 1), row pitch nx + 1
+  double* z[2];     // iterates (ping-pong); boundary entries stay zero
+  double* b;        // right-hand side (coarse levels)
+};
+
+struct PStats {
+  int iters, status;
+  double rr, ff, rr_true;
+};
+
+struct PDesc {
+  int L, fl;                 // finest level; levels 0..fl run on CTA 0 alone
+  int mode, nu1, nu2, max_it;
+  double tol2, wd;           // tol^2, omega / D = 3 omega / 8
+  int n0;                    // interior nodes of the coarsest grid
+  const double* Kinv;        // n0 x n0, row-major
+  const double* f;           // finest right-hand side / input vector (nodal layout)
+  double* x;                 // finest iterate (solve), output (precond / apply)
+  double *r, *p, *q;         // finest CG vectors
+  PStats* stats;
+  PLevel lv[PMAXL];
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double nbsum(const double* z, int k, int pitch) {
+  return (z[k - pitch - 1] + z[k - pitch] + z[k - pitch + 1]) + (z[k - 1] + z[k + 1]) +
+         (z[k + pitch - 1] + z[k + pitch] + z[k + pitch + 1]);
+}
+
+// (K z)(k) for the 9-point Q4 stencil.
+__device__ __forceinline__ double apply_k(const double* z, int k, int pitch) {
+  return (8.0 * z[k] - nbsum(z, k, pitch)) * (1.0 / 3.0);
+}
+
+// Bilinear interpolation of the coarse vector zc (pitch pc) at fine node (i, j).
+__device__ __forceinline__ double prolong(const double* zc, int pc, int i, int j) {
+  const int I = i >> 1, J = j >> 1;
+  const int k = J * pc + I;
+  if (!(j & 1)) return (i & 1) ? 0.5 * (zc[k] + zc[k + 1]) : zc[k];
+  if (!(i & 1)) return 0.5 * (zc[k] + zc[k + pc]);
+  return 0.25 * ((zc[k] + zc[k + 1]) + (zc[k + pc] + zc[k + pc + 1]));
+}
+
+// Work split of a phase: this CTA's block of interior node rows [j0, j1) of a
+// level with ny elements in y, and its rank / size (1 for CTA-local phases).
+struct Part {
+  int rank, size;
+};
+
+__device__ __forceinline__ void rows_of(int ny, Part pt, int& j0, int& j1) {
+  const int rows = ny - 1;
+  const int per = (rows + pt.size - 1) / pt.size;
+  j0 = 1 + pt.rank * per;
+  j1 = min(ny, j0 + per);
+}
+
+// Calls fn(i, j, k) for every interior node of this CTA's rows.
+template <typename F> __device__ __forceinline__ void for_nodes(int nx, int ny, Part pt, F fn) {
+  int j0, j1;
+  rows_of(ny, pt, j0, j1);
+  const int w = nx - 1;
+  const int count = (j1 - j0) * w;
+  for (int t = threadIdx.x; t < count; t += PNT) {
+    const int j = j0 + t / w;
+    const int i = 1 + t % w;
+    fn(i, j, j * (nx + 1) + i);
+  }
+}
+
+}  // namespace
+
+namespace {
+
+struct PShared {
+  double red[4][PMAXC];   // all-gathered partial sums, one row per reduction slot
+  double warp[2][PWARPS];
+};
+
+// Reduction slots (each used once per PCG iteration, so that consecutive
+// uses of a slot are separated by several barriers).
+enum { SLOT_RHO = 0, SLOT_PQ = 1, SLOT_RR = 2, SLOT_FF = 3, SLOT_TRUE = 3 };
+
+struct Solver {
+  const PDesc& d;
+  PShared& sh;
+  int rank, C;
+  cg::cluster_group cl;
+
+  __device__ Part part(bool cluster) const { return cluster ? Part{rank, C} : Part{0, 1}; }
+  // Level l is split over the cluster (else it runs in CTA 0 alone).
+  __device__ bool split(int l) const { return C > 1 && l > d.fl; }
+  __device__ void sync(bool cluster) {
+    if (cluster) cl.sync();
+    else __syncthreads();
+  }
+  // Iterate buffers: the pre-smoothed iterate and the final one of level l.
+  __device__ int pre_buf() const { return (d.nu1 - 1) & 1; }
+  __device__ int final_buf(int l) const { return l == 0 ? 0 : (d.nu1 - 1 + d.nu2) & 1; }
+
+  // Sum of a (and b) over the cluster, in rank order; every thread of every
+  // CTA gets the same result.  Includes the phase barrier.
+  __device__ void allreduce(double& a, double& b, int slot_a, int slot_b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      sh.warp[0][w] = a;
+      sh.warp[1][w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0.0, sb = 0.0;
+      for (int i = 0; i < PWARPS; ++i) {
+        sa += sh.warp[0][i];
+        sb += sh.warp[1][i];
+      }
+      if (C > 1) {
+        for (int dst = 0; dst < C; ++dst) {
+          cl.map_shared_rank(&sh.red[slot_a][0], dst)[rank] = sa;
+          if (slot_b >= 0) cl.map_shared_rank(&sh.red[slot_b][0], dst)[rank] = sb;
+        }
+      } else {
+        sh.red[slot_a][0] = sa;
+        if (slot_b >= 0) sh.red[slot_b][0] = sb;
+      }
+    }
+    sync(C > 1);
+    a = 0.0;
+    b = 0.0;
+    for (int i = 0; i < C; ++i) {
+      a += sh.red[slot_a][i];
+      if (slot_b >= 0) b += sh.red[slot_b][i];
+    }
+  }
+  __device__ double allreduce1(double a, int slot) {
+    double b = 0.0;
+    allreduce(a, b, slot, -1);
+    return a;
+  }
+
+  // dst = src + (omega / D)(b - K src) on level l; returns the sum of
+  // dst * dotv over this CTA's nodes (dotv may be null).
+  __device__ double sweep(int l, const double* src, double* dst, const double* b, bool cluster,
+                          const double* dotv) {
+    const PLevel& lv = d.lv[l];
+    const int pitch = lv.nx + 1;
+    const double wd = d.wd;
+    double acc = 0.0;
+    for_nodes(lv.nx, lv.ny, part(cluster), [&](int, int, int k) {
+      const double zk = src[k];
+      const double v = zk + wd * (b[k] - (8.0 * zk - nbsum(src, k, pitch)) * (1.0 / 3.0));
+      dst[k] = v;
+      if (dotv) acc = fma(v, dotv[k], acc);
+    });
+    return acc;
+  }
+
+  // The prolongation and correction z = zpre + P zc fused with the first
+  // post-smoothing sweep: the corrected iterate is formed on the fly at the
+  // node and its eight neighbours.
+  __device__ double prolong_sweep(int l, const double* zpre, const double* zc, double* dst,
+                                  const double* b, bool cluster, const double* dotv) {
+    const PLevel& lv = d.lv[l];
+    const int pitch = lv.nx + 1, pc = d.lv[l - 1].nx + 1;
+    const double wd = d.wd;
+    double acc = 0.0;
+    for_nodes(lv.nx, lv.ny, part(cluster), [&](int i, int j, int k) {
+      auto zf = [&](int di, int dj) {
+        return zpre[k + dj * pitch + di] + prolong(zc, pc, i + di, j + dj);
+      };
+      const double s = (zf(-1, -1) + zf(0, -1) + zf(1, -1)) + (zf(-1, 0) + zf(1, 0)) +
+                       (zf(-1, 1) + zf(0, 1) + zf(1, 1));
+      const double zk = zf(0, 0);
+      const double v = zk + wd * (b[k] - (8.0 * zk - s) * (1.0 / 3.0));
+      dst[k] = v;
+      if (dotv) acc = fma(v, dotv[k], acc);
+    });
+    return acc;
+  }
+
+  // Full-weighting restriction R = P^T of the residual b - K zpre of level l
+  // (formed on the fly at the nine fine nodes of each coarse node) into the
+  // right-hand side of level l - 1, and that level's first smoothing step
+  // from zero, z = (omega / D) b (pointwise), unless it is the coarsest grid.
+  __device__ void restrict_to(int l, const double* zpre, const double* b, bool cluster) {
+    const PLevel& f = d.lv[l];
+    const PLevel& c = d.lv[l - 1];
+    const int pf = f.nx + 1;
+    const double wd = d.wd;
+    const bool z0 = l - 1 >= 1;
+    for_nodes(c.nx, c.ny, part(cluster), [&](int I, int J, int kc) {
+      const int k = 2 * J * pf + 2 * I;
+      auto res = [&](int kk) { return b[kk] - (8.0 * zpre[kk] - nbsum(zpre, kk, pf)) * (1.0 / 3.0); };
+      const double s = res(k) + 0.5 * ((res(k - 1) + res(k + 1)) + (res(k - pf) + res(k + pf))) +
+                       0.25 * ((res(k - pf - 1) + res(k - pf + 1)) + (res(k + pf - 1) + res(k + pf + 1)));
+      c.b[kc] = s;
+      if (z0) c.z[0][kc] = wd * s;
+    });
+  }
+
+  // Coarsest grid: z = K_0^-1 b (one warp per row of the dense inverse).
+  __device__ void coarsest() {
+    const PLevel& c = d.lv[0];
+    const int n = d.n0, w = c.nx - 1, pitch = c.nx + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = warp; a < n; a += PWARPS) {
+      double s = 0.0;
+      for (int bb = lane; bb < n; bb += 32)
+        s = fma(d.Kinv[(size_t)a * n + bb], c.b[(1 + bb / w) * pitch + 1 + bb % w], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) c.z[0][(1 + a / w) * pitch + 1 + a % w] = s;
+    }
+  }
+
+  // Pre-smoothing (the first step from zero is already in z[0]) and the
+  // restriction of level l.
+  __device__ void descend(int l, const double* b, bool cluster) {
+    const PLevel& lv = d.lv[l];
+    int cur = 0;
+    for (int s = 1; s < d.nu1; ++s) {
+      sweep(l, lv.z[cur], lv.z[cur ^ 1], b, cluster, nullptr);
+      cur ^= 1;
+      sync(cluster);
+    }
+    restrict_to(l, lv.z[cur], b, cluster);
+    sync(cluster);
+  }
+
+  // Prolongation, correction and post-smoothing of level l.  With dotv, the
+  // last sweep also forms the partial z . dotv and its barrier is left to
+  // the reduction that follows.
+  __device__ double ascend(int l, const double* b, bool cluster, const double* dotv) {
+    const PLevel& lv = d.lv[l];
+    const double* zc = d.lv[l - 1].z[final_buf(l - 1)];
+    int cur = pre_buf();
+    double acc = prolong_sweep(l, lv.z[cur], zc, lv.z[cur ^ 1], b, cluster,
+                               d.nu2 == 1 ? dotv : nullptr);
+    cur ^= 1;
+    for (int s = 1; s < d.nu2; ++s) {
+      sync(cluster);
+      acc += sweep(l, lv.z[cur], lv.z[cur ^ 1], b, cluster, s == d.nu2 - 1 ? dotv : nullptr);
+      cur ^= 1;
+    }
+    if (!dotv) sync(cluster);
+    return acc;
+  }
+
+  // One V-cycle (Alg. 1 with gamma = 1) for the finest right-hand side bL,
+  // whose first smoothing step is already in lv[L].z[0].  Returns this CTA's
+  // part of z . dotv when dotv is given (the caller reduces it).
+  __device__ double vcycle(const double* bL, const double* dotv) {
+    const int L = d.L;
+    const int top_local = C > 1 ? d.fl : L;
+    for (int l = L; l > top_local; --l) descend(l, l == L ? bL : d.lv[l].b, true);
+    double acc = 0.0;
+    if (C == 1 || rank == 0) {
+      for (int l = top_local; l >= 1; --l) descend(l, l == L ? bL : d.lv[l].b, false);
+      coarsest();
+      __syncthreads();
+      for (int l = 1; l <= top_local; ++l)
+        acc += ascend(l, l == L ? bL : d.lv[l].b, false, l == L ? dotv : nullptr);
+    }
+    if (C > 1) cl.sync();
+    for (int l = top_local + 1; l <= L; ++l)
+      acc += ascend(l, l == L ? bL : d.lv[l].b, true, l == L ? dotv : nullptr);
+    return acc;
+  }
+
+  // ------------------------------------------------------------------------
+  // Alg. 2 with the V-cycle above as preconditioner, Fletcher-Reeves beta;
+  // stop when ||r|| <= tol ||f|| (tested before the preconditioner).
+  // q = K p is formed as K z + beta q (K is linear), so that the phase needs
+  // z at the neighbours (complete after the V-cycle's last barrier) but p
+  // only at the node itself.
+  // ------------------------------------------------------------------------
+  __device__ void solve() {
+    const PLevel& F = d.lv[d.L];
+    const int nx = F.nx, ny = F.ny, pitch = nx + 1;
+    const bool cl_on = C > 1;
+    const Part pt = part(cl_on);
+    double* x = d.x;
+    double *r = d.r, *p = d.p, *q = d.q;
+    const double* f = d.f;
+    double* z0 = F.z[0];
+    const double wd = d.wd;
+    // Warm start: the iterate is zero on the boundary.
+    if (rank == 0) {
+      for (int t = threadIdx.x; t < nx + 1; t += PNT) {
+        x[t] = 0.0;
+        x[ny * pitch + t] = 0.0;
+      }
+      for (int t = threadIdx.x; t < ny + 1; t += PNT) {
+        x[t * pitch] = 0.0;
+        x[t * pitch + nx] = 0.0;
+      }
+    }
+    sync(cl_on);
+    double rr = 0.0, ff = 0.0;
+    for_nodes(nx, ny, pt, [&](int, int, int k) {
+      const double rk = f[k] - apply_k(x, k, pitch);
+      r[k] = rk;
+      z0[k] = wd * rk;
+      rr = fma(rk, rk, rr);
+      ff = fma(f[k], f[k], ff);
+    });
+    allreduce(rr, ff, SLOT_RR, SLOT_FF);
+    int it = 0, status = PST_RUNNING;
+    double rho_old = 1.0;
+    const double* z = F.z[final_buf(d.L)];
+    for (;;) {
+      if (!isfinite(rr)) {
+        status = PST_BREAKDOWN;
+        break;
+      }
+      if (rr <= d.tol2 * ff) {
+        status = PST_CONVERGED;
+        break;
+      }
+      if (it >= d.max_it) {
+        status = PST_MAXIT;
+        break;
+      }
+      const double rho = allreduce1(vcycle(r, r), SLOT_RHO);
+      if (!(rho > 0.0) || !isfinite(rho)) {
+        status = PST_BREAKDOWN;
+        break;
+      }
+      const double beta = it == 0 ? 0.0 : rho / rho_old;
+      double pq = 0.0;
+      for_nodes(nx, ny, pt, [&](int, int, int k) {
+        const double kz = apply_k(z, k, pitch);
+        const double pk = it == 0 ? z[k] : fma(beta, p[k], z[k]);
+        const double qk = it == 0 ? kz : fma(beta, q[k], kz);
+        p[k] = pk;
+        q[k] = qk;
+        pq = fma(pk, qk, pq);
+      });
+      pq = allreduce1(pq, SLOT_PQ);
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        status = PST_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / pq;
+      double rn = 0.0;
+      for_nodes(nx, ny, pt, [&](int, int, int k) {
+        x[k] = fma(alpha, p[k], x[k]);
+        const double rk = fma(-alpha, q[k], r[k]);
+        r[k] = rk;
+        z0[k] = wd * rk;  // the next V-cycle's first smoothing step from zero
+        rn = fma(rk, rk, rn);
+      });
+      rr = allreduce1(rn, SLOT_RR);
+      rho_old = rho;
+      ++it;
+    }
+    // True residual of the returned iterate.
+    double rt = 0.0;
+    for_nodes(nx, ny, pt, [&](int, int, int k) {
+      const double rk = f[k] - apply_k(x, k, pitch);
+      rt = fma(rk, rk, rt);
+    });
+    rt = allreduce1(rt, SLOT_TRUE);
+    if (rank == 0 && threadIdx.x == 0) {
+      d.stats->iters = it;
+      d.stats->status = status;
+      d.stats->rr = rr;
+      d.stats->ff = ff;
+      d.stats->rr_true = rt;
+    }
+  }
+
+  // z = one V-cycle applied to the input vector (the preconditioner alone).
+  __device__ void precondition() {
+    const PLevel& F = d.lv[d.L];
+    const bool cl_on = C > 1;
+    const double wd = d.wd;
+    const double* v = d.f;
+    double* z0 = F.z[0];
+    for_nodes(F.nx, F.ny, part(cl_on), [&](int, int, int k) { z0[k] = wd * v[k]; });
+    sync(cl_on);
+    vcycle(v, nullptr);
+    const double* z = F.z[final_buf(d.L)];
+    copy_out(z);
+  }
+
+  // y = K v with v read as zero on the boundary.
+  __device__ void apply() {
+    const PLevel& F = d.lv[d.L];
+    const int nx = F.nx, ny = F.ny, pitch = nx + 1;
+    const double* v = d.f;
+    double* y = d.x;
+    for_nodes(nx, ny, part(C > 1), [&](int i, int j, int k) {
+      auto vv = [&](int di, int dj) {
+        const int ii = i + di, jj = j + dj;
+        return (ii == 0 || ii == nx || jj == 0 || jj == ny) ? 0.0 : v[k + dj * pitch + di];
+      };
+      const double s = (vv(-1, -1) + vv(0, -1) + vv(1, -1)) + (vv(-1, 0) + vv(1, 0)) +
+                       (vv(-1, 1) + vv(0, 1) + vv(1, 1));
+      y[k] = (8.0 * v[k] - s) * (1.0 / 3.0);
+    });
+    zero_boundary(y);
+    sync(C > 1);
+  }
+
+  // out = z at every node (z is zero on the boundary).
+  __device__ void copy_out(const double* z) {
+    const PLevel& F = d.lv[d.L];
+    const int n = (F.nx + 1) * (F.ny + 1);
+    const int per = (n + C - 1) / C;
+    const int a = rank * per, e = min(n, a + per);
+    for (int k = a + threadIdx.x; k < e; k += PNT) d.x[k] = z[k];
+    sync(C > 1);
+  }
+
+  __device__ void zero_boundary(double* y) {
+    if (rank != 0) return;
+    const PLevel& F = d.lv[d.L];
+    const int nx = F.nx, ny = F.ny, pitch = nx + 1;
+    for (int t = threadIdx.x; t < nx + 1; t += PNT) {
+      y[t] = 0.0;
+      y[ny * pitch + t] = 0.0;
+    }
+    for (int t = threadIdx.x; t < ny + 1; t += PNT) {
+      y[t * pitch] = 0.0;
+      y[t * pitch + nx] = 0.0;
+    }
+  }
+};
+
+// One cluster of C CTAs per descriptor (right-hand side).
+__global__ void __launch_bounds__(PNT, 1) poisson_cluster_kernel(const PDesc* __restrict__ descs, int C) {
+  __shared__ PDesc sd;
+  __shared__ PShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const PDesc* src = descs + blockIdx.x / C;
+  {
+    const int* s = reinterpret_cast<const int*>(src);
+    int* t = reinterpret_cast<int*>(&sd);
+    for (int i = threadIdx.x; i < (int)(sizeof(PDesc) / sizeof(int)); i += PNT) t[i] = s[i];
+  }
+  __syncthreads();
+  Solver s{sd, sh, rank, C, cl};
+  if (sd.mode == PMODE_SOLVE) s.solve();
+  else if (sd.mode == PMODE_PRECOND) s.precondition();
+  else s.apply();
+}
+
+// Coarsest grid (one CTA): band Cholesky of K_0 (Alg. 3, right-looking, in
+// the lower band Ab[i * (bw + 1) + i - j]), then K_0^-1 column by column by
+// forward and back substitution.  err is set when a pivot is not positive.
+__global__ void __launch_bounds__(PNT) poisson_coarsest_kernel(int nx0, int ny0, double* Ab,
+                                                               double* Kinv, int* err) {
+  const int w = nx0 - 1, n = w * (ny0 - 1), bw = w + 1, ld = bw + 1;
+  for (int t = threadIdx.x; t < n * ld; t += PNT) {
+    const int i = t / ld, dd = t % ld, j = i - dd;
+    double v = 0.0;
+    if (j >= 0) {
+      const int dx = i % w - j % w, dy = i / w - j / w;
+      if (dd == 0) v = 8.0 / 3.0;
+      else if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) v = -1.0 / 3.0;
+    }
+    Ab[t] = v;
+  }
+  __syncthreads();
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double a = Ab[(size_t)k * ld];
+      if (!(a > 0.0)) *err = 1;
+      piv = sqrt(a > 0.0 ? a : 1.0);
+      Ab[(size_t)k * ld] = piv;
+    }
+    __syncthreads();
+    const int m = min(n - 1, k + bw);
+    for (int i = k + 1 + threadIdx.x; i <= m; i += PNT) Ab[(size_t)i * ld + (i - k)] /= piv;
+    __syncthreads();
+    const int cnt = m - k;
+    for (int t = threadIdx.x; t < cnt * cnt; t += PNT) {
+      const int i = k + 1 + t / cnt, j = k + 1 + t % cnt;
+      if (j <= i) Ab[(size_t)i * ld + (i - j)] -= Ab[(size_t)i * ld + (i - k)] * Ab[(size_t)j * ld + (j - k)];
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < n; c += PNT) {
+    for (int i = 0; i < n; ++i) {  // L y = e_c
+      double s = i == c ? 1.0 : 0.0;
+      for (int j = max(0, i - bw); j < i; ++j) s -= Ab[(size_t)i * ld + (i - j)] * Kinv[(size_t)j * n + c];
+      Kinv[(size_t)i * n + c] = s / Ab[(size_t)i * ld];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+      double s = Kinv[(size_t)i * n + c];
+      for (int j = i + 1; j <= min(n - 1, i + bw); ++j) s -= Ab[(size_t)j * ld + (j - i)] * Kinv[(size_t)j * n + c];
+      Kinv[(size_t)i * n + c] = s / Ab[(size_t)i * ld];
+    }
+  }
+}
+
+}  // namespace
+
+struct mto_poisson {
+  int device = 0, nelx = 0, nely = 0, L = 0, fl = 0, C = 1, n0 = 0;
+  mto_poisson_opts o{};
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
+  double* Kinv = nullptr;
+  double* Ab = nullptr;
+  int* err = nullptr;
+  // Per right-hand-side workspace (grown on demand): r, p, q of the finest
+  // grid and z[0], z[1], b of every grid, zero on the boundary.
+  int cap = 0;
+  double* ws = nullptr;
+  size_t ws_per_rhs = 0;
+  PDesc* d_desc = nullptr;
+  PStats* d_stats = nullptr;
+  PStats* h_stats = nullptr;  // pinned
+  // Descriptors are staged from pageable memory: the copy call returns once
+  // they have left this buffer, so that a later call may refill it at once.
+  std::vector<PDesc> h_desc;
+  std::vector<int> lvl_nodes;  // nodes of each grid
+  long long launches = 0;
+  mto_solve_stats last{};
+  float ms_setup = 0.f;
+};
+
+namespace {
+
+size_t level_nodes(int nx, int ny) { return (size_t)(nx + 1) * (ny + 1); }
+
+// Workspace offsets (in doubles) of one right-hand side.
+struct WsLayout {
+  size_t r, p, q, z0[PMAXL], z1[PMAXL], b[PMAXL], total;
+};
+WsLayout ws_layout(const mto_poisson* c) {
+  WsLayout w{};
+  size_t off = 0;
+  const size_t nf = c->lvl_nodes[c->L];
+  w.r = off; off += nf;
+  w.p = off; off += nf;
+  w.q = off; off += nf;
+  for (int l = 0; l <= c->L; ++l) {
+    const size_t n = c->lvl_nodes[l];
+    w.z0[l] = off; off += n;
+    w.z1[l] = off; off += n;
+    w.b[l] = off; off += n;
+  }
+  w.total = (off + 31) & ~(size_t)31;  // 256-byte aligned slices
+  return w;
+}
+
+mto_status fail_cuda(cudaError_t e) {
+  mto::g_last_cuda = e;
+  cudaGetLastError();
+  return MTO_ERR_CUDA;
+}
+
+#define PCK(call)                                \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return fail_cuda(e_); \
+  } while (0)
+
+mto_status grow_ws(mto_poisson* c, int n_rhs) {
+  if (n_rhs <= c->cap) return MTO_OK;
+  const WsLayout w = ws_layout(c);
+  double* ws = nullptr;
+  if (cudaMalloc(&ws, sizeof(double) * w.total * n_rhs) != cudaSuccess) {
+    cudaGetLastError();
+    return MTO_ERR_OOM;
+  }
+  // Boundary entries are never written by the kernel: zero them once.
+  if (cudaMemset(ws, 0, sizeof(double) * w.total * n_rhs) != cudaSuccess) {
+    cudaFree(ws);
+    return fail_cuda(cudaGetLastError());
+  }
+  PDesc* dd = nullptr;
+  PStats* ds = nullptr;
+  if (cudaMalloc(&dd, sizeof(PDesc) * n_rhs) != cudaSuccess ||
+      cudaMalloc(&ds, sizeof(PStats) * n_rhs) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ws);
+    if (dd) cudaFree(dd);
+    return MTO_ERR_OOM;
+  }
+  PStats* hs = nullptr;
+  if (cudaMallocHost(&hs, sizeof(PStats) * n_rhs) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ws);
+    cudaFree(dd);
+    cudaFree(ds);
+    return MTO_ERR_OOM;
+  }
+  cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_desc) cudaFree(c->d_desc);
+  if (c->d_stats) cudaFree(c->d_stats);
+  if (c->h_stats) cudaFreeHost(c->h_stats);
+  c->ws = ws;
+  c->d_desc = dd;
+  c->d_stats = ds;
+  c->h_desc.resize(n_rhs);
+  c->h_stats = hs;
+  c->ws_per_rhs = w.total;
+  c->cap = n_rhs;
+  return MTO_OK;
+}
+
+// Descriptor of right-hand side k.
+PDesc make_desc(const mto_poisson* c, int k, int mode, const double* in, double* out) {
+  const WsLayout w = ws_layout(c);
+  double* base = c->ws + c->ws_per_rhs * k;
+  PDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.L = c->L;
+  d.fl = c->fl;
+  d.mode = mode;
+  d.nu1 = c->o.nu1;
+  d.nu2 = c->o.nu2;
+  d.max_it = c->o.max_it;
+  d.tol2 = c->o.tol * c->o.tol;
+  d.wd = c->o.omega * 3.0 / 8.0;
+  d.n0 = c->n0;
+  d.Kinv = c->Kinv;
+  d.f = in;
+  d.x = out;
+  d.r = base + w.r;
+  d.p = base + w.p;
+  d.q = base + w.q;
+  d.stats = c->d_stats + k;
+  for (int l = 0; l <= c->L; ++l) {
+    const int sh = c->L - l;
+    d.lv[l].nx = c->nelx >> sh;
+    d.lv[l].ny = c->nely >> sh;
+    d.lv[l].z[0] = base + w.z0[l];
+    d.lv[l].z[1] = base + w.z1[l];
+    d.lv[l].b = base + w.b[l];
+  }
+  return d;
+}
+
+// Enqueues one launch: a cluster of C CTAs per right-hand side.
+mto_status launch(mto_poisson* c, int n, int mode, const double* in, double* out, size_t stride) {
+  for (int k = 0; k < n; ++k) c->h_desc[k] = make_desc(c, k, mode, in + stride * k, out + stride * k);
+  PCK(cudaMemcpyAsync(c->d_desc, c->h_desc.data(), sizeof(PDesc) * n, cudaMemcpyHostToDevice,
+                      c->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->C * n);
+  cfg.blockDim = dim3(PNT);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = c->C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  c->launches += 1;
+  PCK(cudaLaunchKernelEx(&cfg, poisson_cluster_kernel, (const PDesc*)c->d_desc, c->C));
+  return MTO_OK;
+}
+
+mto_status enter(mto_poisson* c) {
+  PCK(cudaSetDevice(c->device));
+  PCK(cudaEventRecord(c->ev_in, c->user_stream));
+  PCK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  return MTO_OK;
+}
+
+mto_status leave(mto_poisson* c) {
+  PCK(cudaEventRecord(c->ev_out, c->stream));
+  PCK(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+  return MTO_OK;
+}
+
+// Largest cluster size (power of two, <= want) that the device can schedule
+// for this kernel.
+int usable_cluster(int want) {
+  cudaFuncSetAttribute(poisson_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  for (int C = want; C > 1; C >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(PNT);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, poisson_cluster_kernel, &cfg) == cudaSuccess &&
+        clusters > 0)
+      return C;
+    cudaGetLastError();
+  }
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mto_poisson_default_opts(mto_poisson_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->max_it = 500;
+  o->omega = 0.6;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->n_coarsen = 3;
+  o->cluster_ctas = 0;
+}
+
+void mto_poisson_destroy(mto_poisson* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_desc) cudaFree(c->d_desc);
+  if (c->d_stats) cudaFree(c->d_stats);
+  if (c->h_stats) cudaFreeHost(c->h_stats);
+  if (c->Kinv) cudaFree(c->Kinv);
+  if (c->Ab) cudaFree(c->Ab);
+  if (c->err) cudaFree(c->err);
+  for (cudaEvent_t e : {c->ev_in, c->ev_out, c->ev_a, c->ev_b})
+    if (e) cudaEventDestroy(e);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+static mto_status poisson_create_impl(mto_poisson* c, int device, void* stream) {
+  PCK(cudaSetDevice(device));
+  c->device = device;
+  c->user_stream = static_cast<cudaStream_t>(stream);
+  PCK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  PCK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  PCK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  PCK(cudaEventCreate(&c->ev_a));
+  PCK(cudaEventCreate(&c->ev_b));
+  // Cluster size: one CTA while the finest grid fits one CTA's share of
+  // work, else about one CTA per 4096 interior nodes (a power of two, at
+  // most 16, at most what the device schedules).
+  const long long interior = (long long)(c->nelx - 1) * (c->nely - 1);
+  int want = c->o.cluster_ctas;
+  if (want == 0) {
+    want = 1;
+    while (want < PMAXC && (long long)want * LOCAL_MAX_NODES < interior) want <<= 1;
+  }
+  if (interior <= LOCAL_MAX_NODES) want = 1;
+  c->C = want > 1 ? usable_cluster(want) : 1;
+  // Levels small enough for CTA 0 alone.
+  c->fl = c->L;
+  if (c->C > 1) {
+    c->fl = 0;
+    for (int l = 0; l < c->L; ++l) {
+      const int sh = c->L - l;
+      if ((long long)((c->nelx >> sh) - 1) * ((c->nely >> sh) - 1) <= LOCAL_MAX_NODES) c->fl = l;
+    }
+  }
+  for (int l = 0; l <= c->L; ++l) {
+    const int sh = c->L - l;
+    c->lvl_nodes.push_back((int)level_nodes(c->nelx >> sh, c->nely >> sh));
+  }
+  // Coarsest grid: band Cholesky and explicit inverse on the device.
+  const int nx0 = c->nelx >> c->L, ny0 = c->nely >> c->L;
+  c->n0 = (nx0 - 1) * (ny0 - 1);
+  const int ld = nx0 + 1;  // band width + 1
+  if (cudaMalloc(&c->Kinv, sizeof(double) * (size_t)c->n0 * c->n0) != cudaSuccess ||
+      cudaMalloc(&c->Ab, sizeof(double) * (size_t)c->n0 * ld) != cudaSuccess ||
+      cudaMalloc(&c->err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return MTO_ERR_OOM;
+  }
+  PCK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+  PCK(cudaEventRecord(c->ev_a, c->stream));
+  poisson_coarsest_kernel<<<1, PNT, 0, c->stream>>>(nx0, ny0, c->Ab, c->Kinv, c->err);
+  PCK(cudaGetLastError());
+  c->launches += 1;
+  PCK(cudaEventRecord(c->ev_b, c->stream));
+  int err = 0;
+  PCK(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PCK(cudaStreamSynchronize(c->stream));
+  PCK(cudaEventElapsedTime(&c->ms_setup, c->ev_a, c->ev_b));
+  if (err) return MTO_ERR_BREAKDOWN;
+  return grow_ws(c, 1);
+}
+
+mto_status mto_poisson_create(mto_poisson** out, int nelx, int nely, const mto_poisson_opts* opts,
+                              int device, void* cuda_stream) {
+  if (!out) return MTO_ERR_ARG;
+  *out = nullptr;
+  mto_poisson_opts o;
+  mto_poisson_default_opts(&o);
+  if (opts) o = *opts;
+  const bool cl_ok = o.cluster_ctas == 0 || o.cluster_ctas == 1 || o.cluster_ctas == 2 ||
+                     o.cluster_ctas == 4 || o.cluster_ctas == 8 || o.cluster_ctas == 16;
+  if (nelx < 2 || nely < 2 || device < 0 || !(o.tol >= 0.0) || o.max_it < 0 || !(o.omega > 0.0) ||
+      !(o.omega <= 1.0) || o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.n_coarsen < 1 ||
+      o.n_coarsen >= PMAXL || !cl_ok)
+    return MTO_ERR_ARG;
+  if (nelx % (1 << o.n_coarsen) || nely % (1 << o.n_coarsen)) return MTO_ERR_UNSUPPORTED_MESH;
+  const int nx0 = nelx >> o.n_coarsen, ny0 = nely >> o.n_coarsen;
+  if (nx0 < 2 || ny0 < 2 || (long long)(nx0 - 1) * (ny0 - 1) > PMAX_COARSE ||
+      (long long)(nelx + 1) * (nely + 1) > (1LL << 28))
+    return MTO_ERR_UNSUPPORTED_MESH;
+  mto_poisson* c = new (std::nothrow) mto_poisson();
+  if (!c) return MTO_ERR_OOM;
+  c->nelx = nelx;
+  c->nely = nely;
+  c->o = o;
+  c->L = o.n_coarsen;
+  const mto_status s = poisson_create_impl(c, device, cuda_stream);
+  if (s != MTO_OK) {
+    cudaGetLastError();
+    mto_poisson_destroy(c);
+    return s;
+  }
+  *out = c;
+  return MTO_OK;
+}
+
+mto_status mto_poisson_solve(mto_poisson* c, int n_rhs, const double* f_dev, double* u_dev,
+                             mto_solve_stats* stats) {
+  if (!c || !f_dev || !u_dev || n_rhs < 1 || n_rhs > PMAX_RHS) return MTO_ERR_ARG;
+  mto_status s = enter(c);
+  if (s != MTO_OK) return s;
+  if ((s = grow_ws(c, n_rhs)) != MTO_OK) return s;
+  PCK(cudaEventRecord(c->ev_a, c->stream));
+  if ((s = launch(c, n_rhs, PMODE_SOLVE, f_dev, u_dev, c->lvl_nodes[c->L])) != MTO_OK) return s;
+  PCK(cudaEventRecord(c->ev_b, c->stream));
+  PCK(cudaMemcpyAsync(c->h_stats, c->d_stats, sizeof(PStats) * n_rhs, cudaMemcpyDeviceToHost,
+                      c->stream));
+  PCK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  PCK(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+  mto_status worst = MTO_OK;
+  int total = 0;
+  for (int k = 0; k < n_rhs; ++k) {
+    const PStats& p = c->h_stats[k];
+    total += p.iters;
+    const mto_status sk = p.status == PST_CONVERGED ? MTO_OK
+                          : p.status == PST_MAXIT   ? MTO_ERR_NOT_CONVERGED
+                                                    : MTO_ERR_BREAKDOWN;
+    if (sk != MTO_OK && worst == MTO_OK) worst = sk;
+  }
+  const PStats& p = c->h_stats[n_rhs - 1];
+  const double fn = std::sqrt(p.ff);
+  c->last.iters = total;
+  c->last.converged = worst == MTO_OK;
+  c->last.rel_res_rec = fn > 0 ? std::sqrt(p.rr) / fn : 0.0;
+  c->last.rel_res_true = fn > 0 ? std::sqrt(p.rr_true) / fn : 0.0;
+  c->last.ms_solve = ms;
+  c->last.ms_setup = c->ms_setup;
+  if (stats) *stats = c->last;
+  if ((s = leave(c)) != MTO_OK) return s;
+  return worst;
+}
+
+mto_status mto_poisson_apply_operator(mto_poisson* c, const double* v_dev, double* y_dev) {
+  if (!c || !v_dev || !y_dev) return MTO_ERR_ARG;
+  mto_status s = enter(c);
+  if (s != MTO_OK) return s;
+  if ((s = launch(c, 1, PMODE_APPLY, v_dev, y_dev, 0)) != MTO_OK) return s;
+  return leave(c);
+}
+
+mto_status mto_poisson_apply_preconditioner(mto_poisson* c, const double* r_dev, double* z_dev) {
+  if (!c || !r_dev || !z_dev) return MTO_ERR_ARG;
+  mto_status s = enter(c);
+  if (s != MTO_OK) return s;
+  if ((s = launch(c, 1, PMODE_PRECOND, r_dev, z_dev, 0)) != MTO_OK) return s;
+  return leave(c);
+}
+
+mto_status mto_poisson_get_info(mto_poisson* c, int* n_levels, int* coarsest_free, int* cluster_ctas,
+                                long long* launches) {
+  if (!c) return MTO_ERR_ARG;
+  if (n_levels) *n_levels = c->L + 1;
+  if (coarsest_free) *coarsest_free = c->n0;
+  if (cluster_ctas) *cluster_ctas = c->C;
+  if (launches) *launches = c->launches;
+  return MTO_OK;
+}
+
+}  // extern "C"

@@ -72,3 +72,25 @@ def test_argument_validation_needs_no_gpu(libpath):
                                    None) == _lib.ERR_ARG, (gamma, nc)
     assert lib.mto_solve(None, 1, None, None, None) == _lib.ERR_ARG
     assert lib.mto_create_mesh(None, 8, 8, 0.3, 1, None, 0, None) == _lib.ERR_ARG
+
+
+def test_poisson_argument_validation_needs_no_gpu(libpath):
+    import ctypes
+    from paper_2301_07457_gb300 import _lib
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    o = _lib.PoissonOpts()
+    lib.mto_poisson_default_opts(ctypes.byref(o))
+    assert (o.tol, o.max_it, o.omega, o.nu1, o.nu2, o.n_coarsen, o.cluster_ctas) == (1e-8, 500, 0.6, 2, 2, 3, 0)
+    create = lambda nx, ny: lib.mto_poisson_create(ctypes.byref(h), nx, ny, ctypes.byref(o), 0, None)
+    assert create(1, 8) == _lib.ERR_ARG
+    assert create(12, 8) == _lib.ERR_UNSUPPORTED_MESH      # not divisible by 2^3
+    assert create(8, 8) == _lib.ERR_UNSUPPORTED_MESH       # coarsest 1 x 1 has no interior node
+    o.n_coarsen = 1
+    assert create(128, 128) == _lib.ERR_UNSUPPORTED_MESH   # coarsest 63^2 interior nodes > 1024
+    o.n_coarsen, o.cluster_ctas = 3, 3
+    assert create(64, 64) == _lib.ERR_ARG                  # cluster sizes are powers of two <= 16
+    o.cluster_ctas, o.omega = 0, 1.5
+    assert create(64, 64) == _lib.ERR_ARG
+    assert lib.mto_poisson_solve(None, 1, None, None, None) == _lib.ERR_ARG
+    assert lib.mto_poisson_create(None, 8, 8, None, 0, None) == _lib.ERR_ARG
