@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-poisson", action="store_true")
+    ap.add_argument("--no-two-load-cases", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (for profiling)")
     ap.add_argument("--sweep-outer", type=int, default=50)
     ap.add_argument("--study", choices=["levels"], default=None,
@@ -512,6 +513,33 @@ def run_ours(args):
                        "frac": sm_bytes / 1e9 / hbm_peak, "traffic": SMOOTH32_TRAFFIC,
                        "ms_per_launch": sm_ms, "samples": kt["samples"][1], "peak_kind": peak_kind}
 
+    # Two load cases (top-edge and right-edge loads) on the same design:
+    # solved at the same time (two workspaces) and one after the other,
+    # against one load case (device time of mto_solve, median of 3).
+    two_lc = None
+    if not args.no_two_load_cases:
+        from synth import load_right_edge
+        F2 = torch.from_numpy(np.stack([f_np, load_right_edge(n, n)])).to(dev)
+        seq = mto.Mesh(n, n, precision="mixed", rr_every=25, flexible=True, concurrent_rhs=1, **common)
+        seq.set_design(x, EP, PENAL)
+        if not args.no_tune:
+            seq.autotune()
+
+        def med_solve(m, rhs):
+            m.solve(rhs)
+            t = sorted(m.solve(rhs)[1]["ms_solve"] for _ in range(3))
+            return t[1]
+        ms1 = med_solve(mixed, f)
+        ms2c = med_solve(mixed, F2)
+        ms2s = med_solve(seq, F2)
+        Uc, _ = mixed.solve(F2)
+        Us, _ = seq.solve(F2)
+        two_lc = {"ms_one_load_case": ms1, "ms_two_concurrent": ms2c, "ms_two_sequential": ms2s,
+                  "ratio_concurrent_to_one": ms2c / ms1, "ratio_sequential_to_one": ms2s / ms1,
+                  "bit_identical": bool(torch.equal(Uc, Us))}
+        seq.close()
+        del F2, Uc, Us
+
     # End to end through the C ABI with pinned host buffers (right after the
     # device-timed steps, on the same context, before the other workloads).
     e2e = None
@@ -610,7 +638,7 @@ def run_ours(args):
         "fp64": fp64, "speedup_mixed_vs_fp64": (value / fp64["solves_s"]) if fp64 else None,
         "roofline": roofline, "roofline_vcycle": roofline_vcycle, "fp64_peak": fp64_probe,
         "launch_shapes": shapes_mixed, "batched": batched, "mesh_sweep": sweep,
-        "poisson_table1": poisson_t1,
+        "poisson_table1": poisson_t1, "two_load_cases": two_lc,
         "clocks": clocks, "gpu_launches": nlaunch, "e2e": e2e, "cpu_baseline": cpu,
     }
     mixed.close()

@@ -74,6 +74,11 @@ typedef struct {
   int gamma;        /* cycle index of Alg. 1 below the finest grid, 1..4 (1: V-cycle,
                        2: W-cycle); the finest grid calls the next one once.  At most
                        512 coarse-grid calls per cycle (MTO_ERR_ARG otherwise). */
+  int concurrent_rhs; /* 1..4: right-hand sides of one mto_solve solved at the same time, each
+                         with its own vectors, scalars, stream and solve graph (the design data
+                         is shared); more than 1 costs one extra set of solve vectors per slot,
+                         allocated on the first solve with that many right-hand sides.  The
+                         results do not depend on it (bit for bit). */
 } mto_solver_opts;
 
 typedef struct {
@@ -86,7 +91,8 @@ typedef struct {
 } mto_solve_stats;
 
 /* Fills the defaults: tol 1e-8, max_it 500, omega 0.6, nu1 = nu2 = 2,
- * n_coarsen 3, Galerkin, FP64, rr_every 25, flexible 0, check_every 4, gamma 1. */
+ * n_coarsen 3, Galerkin, FP64, rr_every 25, flexible 0, check_every 4, gamma 1,
+ * concurrent_rhs 2. */
 void mto_default_opts(mto_solver_opts* opts);
 
 /* Creates a context for an nelx x nely mesh with Poisson ratio nu and the

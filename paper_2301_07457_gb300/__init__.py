@@ -67,7 +67,7 @@ class Mesh:
     def __init__(self, nelx, nely, nu=0.3, fixed_edges=EDGE_BOTTOM, n_coarsen=3,
                  precision="fp64", tol=1e-8, max_it=500, omega=0.6, nu1=2, nu2=2,
                  coarse_kind="galerkin", rr_every=25, flexible=None, check_every=4,
-                 gamma=1, device=None):
+                 gamma=1, concurrent_rhs=2, device=None):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         o = _lib.default_opts()
@@ -79,6 +79,7 @@ class Mesh:
         o.flexible = int(precision == "mixed") if flexible is None else int(flexible)
         o.check_every = check_every
         o.gamma = gamma
+        o.concurrent_rhs = concurrent_rhs
         self.opts = o
         self.nelx, self.nely, self.nu, self.fixed_edges = nelx, nely, nu, fixed_edges
         self.precision = precision

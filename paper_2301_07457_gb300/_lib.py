@@ -44,6 +44,7 @@ class SolverOpts(ctypes.Structure):
         ("flexible", ctypes.c_int),
         ("check_every", ctypes.c_int),
         ("gamma", ctypes.c_int),
+        ("concurrent_rhs", ctypes.c_int),
     ]
 
 

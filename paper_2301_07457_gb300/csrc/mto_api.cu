@@ -70,6 +70,7 @@ void invalidate_graphs(mto_ctx* c) {
   if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
   c->gexec = nullptr;
   c->solve_exec = nullptr;
+  for (mto_ctx* s : c->slots) invalidate_graphs(s);
 }
 
 }  // namespace mto
@@ -492,6 +493,7 @@ bool valid_opts(const mto_solver_opts& o) {
          (o.coarse_kind == MTO_COARSE_GALERKIN || o.coarse_kind == MTO_COARSE_REDISCRETIZE) &&
          (o.precision == MTO_PRECISION_FP64 || o.precision == MTO_PRECISION_MIXED) &&
          o.rr_every >= 0 && o.check_every >= 1 && o.gamma >= 1 && o.gamma <= 4 &&
+         o.concurrent_rhs >= 1 && o.concurrent_rhs <= MAX_CONCURRENT_RHS &&
          coarse_visits(o.n_coarsen, o.gamma) <= MAX_COARSE_VISITS;
 }
 
@@ -700,6 +702,112 @@ mto_status set_design_sync(mto_ctx* c, int n_phase, const double* x_dev, const d
   return MTO_OK;
 }
 
+// Reduction scratch: two partials per block of the largest launch.
+size_t partials_count(const mto_ctx* c) {
+  const Grid& gf = c->lv[c->L].g;
+  int maxb = vec_blocks(gf.size(), c->num_sms);
+  for (int mode = 0; mode <= MODE_RESTRICT; ++mode) {
+    for (int cols = 1; cols <= 2; ++cols) {
+      const SweepShape s = sweep_shape(gf, mode, MAX_TARGET_WARPS_PER_SM * c->num_sms, cols);
+      if (s.nblocks > maxb) maxb = s.nblocks;
+    }
+  }
+  return 2 * (size_t)maxb + 2;
+}
+
+// A workspace for one more concurrent right-hand side: the design data of c
+// is shared (read only during a solve), the solve's vectors, scalars,
+// streams and graphs are its own.  Its rhs_stats point into c's, so that
+// every right-hand side records its statistics in c's array.
+mto_status make_slot(mto_ctx* c, mto_ctx** out) {
+  *out = nullptr;
+  mto_ctx* s = new (std::nothrow) mto_ctx();
+  if (!s) return MTO_ERR_OOM;
+  auto fail = [&](mto_status st) {
+    cudaGetLastError();
+    mto_destroy(s);
+    return st;
+  };
+  s->parent = c;
+  s->device = c->device;
+  s->num_sms = c->num_sms;
+  s->nelx = c->nelx;
+  s->nely = c->nely;
+  s->nu = c->nu;
+  s->fixed = c->fixed;
+  s->o = c->o;
+  s->L = c->L;
+  s->mixed = c->mixed;
+  s->kf64 = c->kf64;
+  s->kf32 = c->kf32;
+  s->w_over_kdiag = c->w_over_kdiag;
+  s->n0 = c->n0;
+  s->bw0 = c->bw0;
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_slot, cudaEventDisableTiming) != cudaSuccess)
+    return fail(MTO_ERR_CUDA);
+  s->cs = s->stream;
+  // Shared design data.
+  s->lv.resize(c->L + 1);
+  for (int l = 0; l <= c->L; ++l) {
+    s->lv[l].g = c->lv[l].g;
+    s->lv[l].coef = c->lv[l].coef;
+    s->lv[l].invd2 = c->lv[l].invd2;
+    s->lv[l].mom = c->lv[l].mom;
+    s->lv[l].coef64 = c->lv[l].coef64;
+  }
+  s->E64 = c->E64;
+  s->Ek4 = c->Ek4;
+  s->Ebf = c->Ebf;
+  s->invd1 = c->invd1;
+  s->dof_index = c->dof_index;
+  s->Kd = c->Kd;
+  s->Kinv = c->Kinv;
+  s->invL = c->invL;
+  s->Lsc = c->Lsc;
+  s->err_flag = c->err_flag;
+  s->rhs_stats = c->rhs_stats;
+  // Own solve data.
+  const size_t vsz = c->mixed ? sizeof(float2) : sizeof(double2);
+  mto_status st = MTO_OK;
+  for (int l = 0; l <= c->L && st == MTO_OK; ++l) {
+    const size_t n = (size_t)s->lv[l].g.size();
+    st = dalloc(s, &s->lv[l].z[0], n * vsz);
+    if (st == MTO_OK) st = dalloc(s, &s->lv[l].z[1], n * vsz);
+    if (st == MTO_OK && l < c->L) st = dalloc(s, &s->lv[l].b, n * vsz);
+  }
+  const size_t nf = (size_t)s->lv[c->L].g.size();
+  if (st == MTO_OK && c->mixed) st = dalloc_t(s, &s->r32, nf);
+  if (st == MTO_OK && c->mixed) st = dalloc_t(s, &s->r_alt, nf);
+  double2** vecs[] = {&s->x, &s->r, &s->q, &s->f, &s->tmp, &s->p[0], &s->p[1]};
+  for (double2** v : vecs)
+    if (st == MTO_OK) st = dalloc_t(s, v, nf);
+  if (st == MTO_OK) st = dalloc_t(s, &s->partials, partials_count(c));
+  if (st == MTO_OK) st = dalloc_t(s, &s->ticket, 4);
+  if (st == MTO_OK) st = dalloc_t(s, &s->sc, 1);
+  if (st != MTO_OK) return fail(st);
+  *out = s;
+  return MTO_OK;
+}
+
+// Design state and launch shapes of c, for a slot's next solve; a change of
+// shape drops the slot's captured graph.
+void sync_slot(const mto_ctx* c, mto_ctx* s) {
+  bool same = s->tw64 == c->tw64;
+  for (int l = 0; l < MAX_LEVELS; ++l) same = same && s->tw[l] == c->tw[l];
+  if (!same) {
+    invalidate_graphs(s);
+    s->tw64 = c->tw64;
+    for (int l = 0; l < MAX_LEVELS; ++l) s->tw[l] = c->tw[l];
+  }
+  s->has_design = c->has_design;
+  s->n_phase = c->n_phase;
+  s->ph = c->ph;
+  s->penal = c->penal;
+  s->ipenal = c->ipenal;
+}
+
 // Solves right-hand sides [0, n_rhs) and fills c->last; one host sync.
 mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) {
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
@@ -713,18 +821,54 @@ mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) 
       cudaGetLastError();
     }
   }
+  // Right-hand sides at the same time (device-side loop only): right-hand
+  // side k runs on workspace k mod S (0: this context), each on its own
+  // stream, forked from and joined back into the context's stream.
+  int S = (c->timing || c->no_while) ? 1 : std::min(n_rhs, c->o.concurrent_rhs);
+  while ((int)c->slots.size() < S - 1) {
+    mto_ctx* w = nullptr;
+    const mto_status st = make_slot(c, &w);
+    if (st == MTO_ERR_OOM) {  // fewer concurrent right-hand sides
+      S = (int)c->slots.size() + 1;
+      break;
+    }
+    if (st != MTO_OK) return st;
+    c->slots.push_back(w);
+  }
+  for (int k = 1; k < S; ++k) {
+    mto_ctx* w = c->slots[k - 1];
+    sync_slot(c, w);
+    if (build_solve_graph(w) != MTO_OK) {  // run them one after another instead
+      cudaGetLastError();
+      S = k;
+      break;
+    }
+  }
+  if (S > 1 && !c->ev_slot) CK(cudaEventCreateWithFlags(&c->ev_slot, cudaEventDisableTiming));
+  auto slot_of = [&](int k) { return k % S == 0 ? c : c->slots[k % S - 1]; };
   CK(cudaEventRecord(c->ev_a, c->stream));
+  if (S > 1) {
+    CK(cudaEventRecord(c->ev_slot, c->stream));
+    for (int k = 1; k < S; ++k) CK(cudaStreamWaitEvent(c->slots[k - 1]->stream, c->ev_slot, 0));
+  }
   for (int k = 0; k < n_rhs; ++k) {
-    c->cs = c->stream;
-    ST(enqueue_rhs_prologue(c, f_dev + k * nd, u_dev + k * nd));
+    mto_ctx* w = slot_of(k);
+    w->cs = w->stream;
+    ST(enqueue_rhs_prologue(w, f_dev + k * nd, u_dev + k * nd));
     if (c->timing || c->no_while) {
       ST(solve_polled(c));
     } else {
-      CK(cudaGraphLaunch(c->solve_exec, c->stream));
-      c->launches += c->solve_kernels_fixed;
+      CK(cudaGraphLaunch(w->solve_exec, w->stream));
+      w->launches += w->solve_kernels_fixed;
     }
-    ST(enqueue_rhs_epilogue(c, u_dev + k * nd, k));
+    ST(enqueue_rhs_epilogue(w, u_dev + k * nd, k));
   }
+  for (int k = 1; k < S; ++k) {
+    mto_ctx* w = c->slots[k - 1];
+    CK(cudaEventRecord(w->ev_slot, w->stream));
+    CK(cudaStreamWaitEvent(c->stream, w->ev_slot, 0));
+  }
+  c->cs = c->stream;
   CK(cudaEventRecord(c->ev_b, c->stream));
   CK(cudaMemcpyAsync(c->rhs_stats_host, c->rhs_stats, sizeof(RhsStats) * n_rhs,
                      cudaMemcpyDeviceToHost, c->stream));
@@ -739,10 +883,14 @@ mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) 
     if (!(c->timing || c->no_while)) {
       // The loop body (two iterations) ran max(1, ceil(iter / 2)) times.
       const long long bodies = r.iter > 0 ? (r.iter + 1) / 2 : 1;
-      c->launches += c->body_kernels * bodies;
+      c->launches += slot_of(k)->body_kernels * bodies;
     }
     const mto_status s = status_of(r);
     if (s != MTO_OK && worst == MTO_OK) worst = s;
+  }
+  for (mto_ctx* w : c->slots) {
+    c->launches += w->launches;
+    w->launches = 0;
   }
   const RhsStats& r = c->rhs_stats_host[n_rhs - 1];
   const double fn = std::sqrt(r.ff);
@@ -777,6 +925,7 @@ void mto_default_opts(mto_solver_opts* o) {
   o->flexible = 0;
   o->check_every = 4;
   o->gamma = 1;
+  o->concurrent_rhs = 2;
 }
 
 const char* mto_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }
@@ -800,6 +949,9 @@ void mto_destroy(mto_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (mto_ctx* s : c->slots) mto_destroy(s);
+  c->slots.clear();
+  if (c->ev_slot) cudaEventDestroy(c->ev_slot);
   invalidate_graphs(c);
   for (void* p : c->allocs) cudaFree(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
@@ -946,15 +1098,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
   ST(dalloc_t(c, &c->Kinv, (size_t)c->n0 * c->n0));
   ST(dalloc_t(c, &c->err_flag, 1));
 
-  // Reduction scratch: two partials per block of the largest launch.
-  int maxb = vec_blocks(gf.size(), c->num_sms);
-  for (int mode = 0; mode <= MODE_RESTRICT; ++mode) {
-    for (int cols = 1; cols <= 2; ++cols) {
-      const SweepShape s = sweep_shape(gf, mode, MAX_TARGET_WARPS_PER_SM * c->num_sms, cols);
-      if (s.nblocks > maxb) maxb = s.nblocks;
-    }
-  }
-  ST(dalloc_t(c, &c->partials, 2 * (size_t)maxb + 2));
+  ST(dalloc_t(c, &c->partials, partials_count(c)));
   ST(dalloc_t(c, &c->ticket, 4));
   ST(dalloc_t(c, &c->sc, 1));
   ST(dalloc_t(c, &c->rhs_stats, MAX_RHS));

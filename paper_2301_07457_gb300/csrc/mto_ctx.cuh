@@ -22,6 +22,8 @@ struct LevelBuf {
 
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_RHS = 64;
+// Right-hand sides of one mto_solve solved at the same time (opts.concurrent_rhs).
+constexpr int MAX_CONCURRENT_RHS = 4;
 // Launch shapes: warps a sweep exposes, per SM (upper end of the tuner's
 // range).  Target 0 means one full wave of the kernel: its resident blocks
 // per SM times the SM count (the default).
@@ -122,6 +124,13 @@ struct mto_ctx {
   float ms_setup = 0.f;
   mto_solve_stats last{};
   std::vector<void*> allocs;
+  // Concurrent right-hand sides: workspaces that share this context's design
+  // data (moduli, smoother diagonals, coarse operators, coarsest inverse) and
+  // own the solve's vectors, scalars, streams and solve graph.  Created on the
+  // first solve with two or more right-hand sides; `parent` is set in them.
+  std::vector<mto_ctx*> slots;
+  mto_ctx* parent = nullptr;
+  cudaEvent_t ev_slot = nullptr;
 };
 
 namespace mto {
