@@ -20,10 +20,12 @@ primitives):
                     sensitivity dC/dx_{e,i} = -p x^{p-1} E_i u_e^T KE u_e.
   * precision    -- round-to-nearest-even to bfloat16, for the mixed path.
   * solver       -- the whole pCGMG solve wired from the pieces above.
+  * poisson      -- the scalar Poisson problem of Sec. 5.1 (Q4 Laplacian,
+                    u = 0 on the boundary) on the same Alg. 1 / Alg. 2 pieces.
 
 Every function names the passage of the paper it follows.  Readings of the
 paper where it is silent or garbled are listed in the project's design notes;
 the ones that change arithmetic are repeated in the docstrings here.
 """
 
-from . import cholesky, fem, multigrid, pcg, precision, sensitivity, solver  # noqa: F401
+from . import cholesky, fem, multigrid, pcg, poisson, precision, sensitivity, solver  # noqa: F401
