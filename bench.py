@@ -80,8 +80,10 @@ def parse():
     ap.add_argument("--study", choices=["levels"], default=None,
                     help="instead of the bench line: pCGMG level study on the paper's meshes")
     ap.add_argument("--study-precision", choices=["fp64", "mixed"], default="fp64")
-    ap.add_argument("--study-outer", type=int, default=100,
+    ap.add_argument("--study-outer", type=int, default=500,
                     help="level study: most outer optimiser iterations per mesh and level")
+    ap.add_argument("--study-seconds", type=float, default=150.0,
+                    help="level study: wall-time budget of the optimiser loop per mesh and level")
     return ap.parse_args()
 
 
@@ -706,10 +708,11 @@ def run_level_study(args):
             opt = ActivePhaseOptimizer(mesh, T["E"], T["V"], f, penal=T["penal"], rf=T["rf"])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            met = opt.run_until(T["tol"], args.study_outer)
+            why = opt.run_until(T["tol"], args.study_outer, args.study_seconds)
             torch.cuda.synchronize()
             its = [h[3] for h in opt.history]
-            row["optimiser"] = {"outer": opt.iteration, "stopped_by_tol": met, "solves": len(its),
+            row["optimiser"] = {"outer": opt.iteration, "stopped_by": why, "last_change": opt.change,
+                                "solves": len(its),
                                 "pcg_iters_mean": sum(its) / len(its), "pcg_iters_max": max(its),
                                 "seconds": time.perf_counter() - t0, "compliance": opt.history[-1][2]}
             mesh.close()

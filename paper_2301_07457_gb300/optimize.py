@@ -17,8 +17,8 @@ steps below are this library's reading of it:
     H_ef = max(0, rf - |c_e - c_f|), with x = x_a;
   * optimality-criteria step with move limit m and damping eta:
     x_a <- clip(x_a (max(0, -d) / lam)^eta, max(eps, x_a - m), min(s - eps, x_a + m)),
-    with lam found by bisection (on the device) so that the phase-a volume
-    equals V_a; then x_b = s - x_a;
+    with lam found on the device (a bracketing search in log(lam)) so that
+    the phase-a volume equals V_a; then x_b = s - x_a;
   * stopping rule (Table 2 gives a tolerance as the optimiser's only stopping
     criterion): stop after the outer iteration in which no phase fraction of
     any element changed by more than tol.
@@ -58,28 +58,33 @@ def filter_sensitivity(d, x, H):
     return (num / (torch.clamp(x.to(torch.float32), min=1e-3) * den)).to(d.dtype)
 
 
-def oc_update(xa, s, d, target, move=0.2, eta=0.5, eps=1e-3, iters=80):
+def oc_update(xa, s, d, target, move=0.2, eta=0.5, eps=1e-3, rounds=10, candidates=16):
     """Optimality-criteria step for phase a of a pair with fixed per-element sum s.
 
-    Returns new x_a with mean(x_a) == target (to bisection accuracy) and
+    Returns new x_a with mean(x_a) == target (to the search's accuracy) and
     eps <= x_a <= s - eps where s > 2 eps (elements with s <= 2 eps keep s/2).
+
+    The multiplier is searched on log(lam) in [-60, 60], all on the device: the
+    volume is non-increasing in lam, so each round evaluates it at `candidates`
+    + 1 points of the current bracket at once and keeps the sub-interval where
+    it crosses the target (10 rounds of 16: a bracket of 1.1e-10 in log(lam)).
     """
     lo_b = torch.clamp(xa - move, min=eps)
     hi_b = torch.clamp(torch.minimum(xa + move, s - eps), min=eps)
     lo_b = torch.minimum(lo_b, hi_b)
-    Bd = torch.clamp(-d, min=0.0)
-    # Bisection on log(lam), all on the device: the volume is decreasing in lam.
-    lmin = torch.tensor(-60.0, dtype=xa.dtype, device=xa.device)
-    lmax = torch.tensor(60.0, dtype=xa.dtype, device=xa.device)
-    xnew = xa
-    for _ in range(iters):
-        lmid = 0.5 * (lmin + lmax)
-        xnew = torch.clamp(xa * (Bd * torch.exp(-lmid)) ** eta, min=0.0)
-        xnew = torch.minimum(torch.maximum(xnew, lo_b), hi_b)
-        too_big = xnew.mean() > target
-        lmin = torch.where(too_big, lmid, lmin)
-        lmax = torch.where(too_big, lmax, lmid)
-    return xnew
+    base = xa * torch.clamp(-d, min=0.0) ** eta  # x(lam) = base * lam^-eta before the bounds
+    frac = torch.linspace(0.0, 1.0, candidates + 1, dtype=xa.dtype, device=xa.device)
+    lo = torch.tensor(-60.0, dtype=xa.dtype, device=xa.device)
+    hi = torch.tensor(60.0, dtype=xa.dtype, device=xa.device)
+    flat_b, flat_lo, flat_hi = base.reshape(1, -1), lo_b.reshape(1, -1), hi_b.reshape(1, -1)
+    for _ in range(rounds):
+        grid = lo + (hi - lo) * frac
+        xs = torch.minimum(torch.maximum(flat_b * torch.exp(-eta * grid)[:, None], flat_lo), flat_hi)
+        too_big = (xs.mean(dim=1) > target).sum()
+        j = torch.clamp(too_big - 1, 0, candidates - 1)
+        lo, hi = grid[j], grid[j + 1]
+    lam = 0.5 * (lo + hi)
+    return torch.minimum(torch.maximum(base * torch.exp(-eta * lam), lo_b), hi_b)
 
 
 class ActivePhaseOptimizer:
@@ -135,14 +140,19 @@ class ActivePhaseOptimizer:
             self.step()
         return self.history
 
-    def run_until(self, tol, max_outer):
+    def run_until(self, tol, max_outer, max_seconds=None):
         """Outer iterations until one changes no fraction by more than tol, at
-        most max_outer of them; returns whether the rule was met."""
+        most max_outer of them and (if given) until max_seconds of wall time
+        have passed; returns why it stopped: "tol", "outer cap" or "time"."""
+        import time
+        t0 = time.perf_counter()
         for _ in range(max_outer):
             self.step()
             if self.change <= tol:
-                return True
-        return False
+                return "tol"
+            if max_seconds is not None and time.perf_counter() - t0 > max_seconds:
+                return "time"
+        return "outer cap"
 
     def state_dict(self):
         return {"x": self.x.cpu(), "u": self.u.cpu(), "iteration": self.iteration,

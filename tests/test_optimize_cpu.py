@@ -75,7 +75,7 @@ def test_stopping_rule_of_the_outer_loop():
     E, V = [9.0, 3.0, 1.0, 1e-9], [0.16, 0.08, 0.08, 0.68]
     f = torch.from_numpy(load_top_edge(12, 8))
     opt = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
-    assert opt.run_until(tol=2e-2, max_outer=60)
+    assert opt.run_until(tol=2e-2, max_outer=60) == "tol"
     changes = []
     ref = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
     for _ in range(opt.iteration):
@@ -85,5 +85,9 @@ def test_stopping_rule_of_the_outer_loop():
     assert torch.equal(ref.x, opt.x)
     # A tolerance it cannot meet: exactly max_outer outer iterations.
     opt2 = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
-    assert not opt2.run_until(tol=-1.0, max_outer=3)
+    assert opt2.run_until(tol=-1.0, max_outer=3) == "outer cap"
     assert opt2.iteration == 3 and len(opt2.history) == 18
+    # A wall-time budget ends the loop after the outer iteration that exceeds it.
+    opt3 = ActivePhaseOptimizer(OracleMesh(12, 8), E, V, f, rf=1.5)
+    assert opt3.run_until(tol=-1.0, max_outer=50, max_seconds=0.0) == "time"
+    assert opt3.iteration == 1
