@@ -257,7 +257,8 @@ mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu, int n_phas
  *
  * A solve is ONE kernel launch: each right-hand side is solved by one
  * thread-block cluster (cluster_ctas CTAs; 0 = chosen by mesh size, one CTA
- * up to 4,096 interior nodes, at most 16) that runs the whole PCG loop with
+ * up to 256 interior nodes, else about one per 256, at most 16) that runs the
+ * whole PCG loop with
  * hardware cluster barriers; right-hand sides run as concurrent clusters.
  * --------------------------------------------------------------------------- */
 typedef struct mto_poisson mto_poisson;
@@ -268,7 +269,7 @@ typedef struct {
   int nu1, nu2;      /* pre- and post-smoothing sweeps, 1..16 */
   int n_coarsen;     /* coarsenings (Sec. 5.1 coarsens down to a 2 x 2 grid) */
   int cluster_ctas;  /* 0 (automatic), 1, 2, 4, 8 or 16 CTAs per right-hand side; more than
-                        one only when the finest grid has over 4,096 interior nodes, and at
+                        one only when the finest grid has over 256 interior nodes, and at
                         most what the device can schedule */
 } mto_poisson_opts;
 

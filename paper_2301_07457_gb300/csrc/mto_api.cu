@@ -808,6 +808,32 @@ void sync_slot(const mto_ctx* c, mto_ctx* s) {
   s->ipenal = c->ipenal;
 }
 
+}  // namespace
+
+namespace mto {
+
+mto_status ensure_slots(mto_ctx* c, int want, int* got) {
+  int S = std::max(1, std::min(want, MAX_CONCURRENT_RHS));
+  while ((int)c->slots.size() < S - 1) {
+    mto_ctx* w = nullptr;
+    const mto_status st = make_slot(c, &w);
+    if (st == MTO_ERR_OOM) {  // fewer concurrent right-hand sides
+      S = (int)c->slots.size() + 1;
+      break;
+    }
+    if (st != MTO_OK) return st;
+    c->slots.push_back(w);
+  }
+  if (S > 1 && !c->ev_slot) CK(cudaEventCreateWithFlags(&c->ev_slot, cudaEventDisableTiming));
+  for (int k = 1; k < S; ++k) sync_slot(c, c->slots[k - 1]);
+  *got = S;
+  return MTO_OK;
+}
+
+}  // namespace mto
+
+namespace {
+
 // Solves right-hand sides [0, n_rhs) and fills c->last; one host sync.
 mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) {
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
@@ -824,27 +850,17 @@ mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) 
   // Right-hand sides at the same time (device-side loop only): right-hand
   // side k runs on workspace k mod S (0: this context), each on its own
   // stream, forked from and joined back into the context's stream.
-  int S = (c->timing || c->no_while) ? 1 : std::min(n_rhs, c->o.concurrent_rhs);
-  while ((int)c->slots.size() < S - 1) {
-    mto_ctx* w = nullptr;
-    const mto_status st = make_slot(c, &w);
-    if (st == MTO_ERR_OOM) {  // fewer concurrent right-hand sides
-      S = (int)c->slots.size() + 1;
-      break;
-    }
-    if (st != MTO_OK) return st;
-    c->slots.push_back(w);
-  }
-  for (int k = 1; k < S; ++k) {
-    mto_ctx* w = c->slots[k - 1];
-    sync_slot(c, w);
-    if (build_solve_graph(w) != MTO_OK) {  // run them one after another instead
-      cudaGetLastError();
-      S = k;
-      break;
+  int S = 1;
+  if (!(c->timing || c->no_while)) {
+    ST(ensure_slots(c, std::min(n_rhs, c->o.concurrent_rhs), &S));
+    for (int k = 1; k < S; ++k) {
+      if (build_solve_graph(c->slots[k - 1]) != MTO_OK) {  // one after another instead
+        cudaGetLastError();
+        S = k;
+        break;
+      }
     }
   }
-  if (S > 1 && !c->ev_slot) CK(cudaEventCreateWithFlags(&c->ev_slot, cudaEventDisableTiming));
   auto slot_of = [&](int k) { return k % S == 0 ? c : c->slots[k % S - 1]; };
   CK(cudaEventRecord(c->ev_a, c->stream));
   if (S > 1) {

@@ -66,19 +66,39 @@ mto_status grow_design(mto_ctx* c, int n_phase) {
 }
 
 // One branch of the batch graph: everything a problem needs, on its context's
-// stream (which joined the capture through the fork event).
-mto_status capture_branch(mto_ctx* c, const mto_batch_item& it, const double* E_phase) {
+// stream (which joined the capture through the fork event).  With S > 1
+// workspaces the load cases fork after set_design: load case k on workspace
+// k mod S, each on its own stream, joined back before the compliance.
+mto_status capture_branch(mto_ctx* c, const mto_batch_item& it, const double* E_phase, int S) {
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
   c->cs = c->stream;
   ST(enqueue_set_design(c, it.n_phase, it.x_dev, E_phase, it.penal));
-  for (int k = 0; k < it.n_rhs; ++k) {
-    ST(enqueue_rhs_prologue(c, it.f_dev + k * nd, it.u_dev + k * nd));
-    ST(enqueue_solve_core(c));
-    ST(enqueue_rhs_epilogue(c, it.u_dev + k * nd, k));
+  if (S > 1) {
+    CK(cudaEventRecord(c->ev_slot, c->stream));
+    for (int k = 1; k < S; ++k) CK(cudaStreamWaitEvent(c->slots[k - 1]->stream, c->ev_slot, 0));
   }
+  for (int k = 0; k < it.n_rhs; ++k) {
+    mto_ctx* w = k % S == 0 ? c : c->slots[k % S - 1];
+    w->cs = w->stream;
+    ST(enqueue_rhs_prologue(w, it.f_dev + k * nd, it.u_dev + k * nd));
+    ST(enqueue_solve_core(w));
+    ST(enqueue_rhs_epilogue(w, it.u_dev + k * nd, k));
+  }
+  for (int k = 1; k < S; ++k) {
+    mto_ctx* w = c->slots[k - 1];
+    CK(cudaEventRecord(w->ev_slot, w->stream));
+    CK(cudaStreamWaitEvent(c->stream, w->ev_slot, 0));
+  }
+  c->cs = c->stream;
   if (it.compliance_dev)
     ST(enqueue_compliance(c, it.n_rhs, it.f_dev, it.u_dev, it.compliance_dev, it.dcdx_dev));
   return MTO_OK;
+}
+
+long long slot_launches(const mto_ctx* c) {
+  long long n = 0;
+  for (const mto_ctx* w : c->slots) n += w->launches;
+  return n;
 }
 
 // Launch shapes already measured in this process: (nx, ny, float32?, source,
@@ -137,8 +157,13 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
   BK(cudaEventCreate(&b->ev_b));
   b->join.resize(n, nullptr);
   for (int i = 0; i < n; ++i) BK(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+  // Workspaces for the load cases of each problem (allocated before the
+  // capture: allocation is not allowed while capturing).
+  std::vector<int> slots(n, 1);
   for (int i = 0; i < n; ++i) {
-    const mto_status s = grow_design(b->ctx[i], items[i].n_phase);
+    mto_status s = grow_design(b->ctx[i], items[i].n_phase);
+    if (s == MTO_OK)
+      s = ensure_slots(b->ctx[i], std::min(items[i].n_rhs, b->ctx[i]->o.concurrent_rhs), &slots[i]);
     if (s != MTO_OK) return fail(s);
     BK(cudaStreamSynchronize(b->ctx[i]->stream));
   }
@@ -153,16 +178,20 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
     mto_ctx* c = b->ctx[i];
     ce = cudaStreamWaitEvent(c->stream, b->fork, 0);
     if (ce != cudaSuccess) break;
-    const long long before = c->launches;
-    st = capture_branch(c, b->items[i], b->E_phase[i].data());
-    fixed += c->launches - before;
+    const long long before = c->launches, before_w = slot_launches(c);
+    st = capture_branch(c, b->items[i], b->E_phase[i].data(), slots[i]);
+    fixed += c->launches - before + slot_launches(c) - before_w;
     c->launches = before;
+    for (mto_ctx* w : c->slots) w->launches = 0;
     if (st == MTO_OK) ce = cudaEventRecord(b->join[i], c->stream);
     if (st == MTO_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[i], 0);
   }
   const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
   g_pdl = true;
-  for (mto_ctx* c : b->ctx) c->cs = c->stream;
+  for (mto_ctx* c : b->ctx) {
+    c->cs = c->stream;
+    for (mto_ctx* w : c->slots) w->cs = w->stream;
+  }
   if (st != MTO_OK || ce != cudaSuccess || ee != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     if (st == MTO_OK) g_last_cuda = ce != cudaSuccess ? ce : ee;

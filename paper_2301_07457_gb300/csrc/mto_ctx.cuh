@@ -169,6 +169,11 @@ mto_status enqueue_rhs_epilogue(mto_ctx* c, double* u_dev, int rhs_slot);
 mto_status enqueue_compliance(mto_ctx* c, int n_rhs, const double* f_dev, const double* u_dev,
                               double* compliance_dev, double* dcdx_dev);
 void invalidate_graphs(mto_ctx* c);
+// Makes `want` workspaces usable for concurrent right-hand sides (the context
+// and want - 1 extra ones, created on first use, design state and launch
+// shapes copied from c); *got is how many are usable (fewer if memory runs
+// out).  Allocates: call outside any stream capture.
+mto_status ensure_slots(mto_ctx* c, int want, int* got);
 int target_warps(const mto_ctx* c, int level);
 int target_warps64(const mto_ctx* c);
 

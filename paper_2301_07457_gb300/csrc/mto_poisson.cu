@@ -16,8 +16,8 @@
 // dependent phases with the hardware cluster barrier; scalar reductions are
 // all-gathered through distributed shared memory and summed in rank order,
 // so every CTA holds the same scalars and takes the same branches.  Levels
-// with at most LOCAL_MAX_NODES interior nodes (and the coarsest solve) run
-// inside CTA 0 alone with block barriers.  All vectors live in global memory
+// with at most LOCAL_MAX_NODES (256) interior nodes (and the coarsest solve)
+// run inside CTA 0 alone with block barriers.  All vectors live in global memory
 // (a few MB: L2-resident).  There is no spin-wait: every barrier is a
 // hardware barrier of the block or the cluster.
 #include <cooperative_groups.h>
@@ -33,11 +33,11 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int PNT = 512;                // threads per CTA
+constexpr int PNT = 256;                // threads per CTA (255 registers each)
 constexpr int PWARPS = PNT / 32;
 constexpr int PMAXC = 16;               // CTAs per cluster (non-portable above 8)
 constexpr int PMAXL = 16;               // grids
-constexpr int LOCAL_MAX_NODES = 4096;   // interior nodes of a level run by CTA 0 alone
+constexpr int LOCAL_MAX_NODES = 256;    // interior nodes of a level run by CTA 0 alone
 constexpr int PMAX_COARSE = 1024;       // interior nodes of the coarsest grid (dense inverse)
 constexpr int PMAX_RHS = 64;
 
@@ -101,6 +101,37 @@ __device__ __forceinline__ void rows_of(int ny, Part pt, int& j0, int& j1) {
   const int per = (rows + pt.size - 1) / pt.size;
   j0 = 1 + pt.rank * per;
   j1 = min(ny, j0 + per);
+}
+
+// For every interior node of this CTA's rows: v = ld(i, j, k), then st(k, v).
+// Each thread takes NB nodes at a time and evaluates ld (loads and
+// arithmetic, no stores) for all of them before the first st, so that the
+// loads of the NB nodes are in flight together: a phase then costs about
+// nodes / (NB * threads) memory round trips instead of nodes / threads.
+template <int NB, typename Ld, typename St>
+__device__ __forceinline__ void for_nodes_nb(int nx, int ny, Part pt, Ld ld, St st) {
+  int j0, j1;
+  rows_of(ny, pt, j0, j1);
+  const int w = nx - 1;
+  const int count = (j1 - j0) * w;
+  for (int t0 = threadIdx.x; t0 < count; t0 += NB * PNT) {
+    decltype(ld(0, 0, 0)) v[NB];
+    int ks[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int t = t0 + u * PNT;
+      ks[u] = -1;
+      if (t < count) {
+        const int j = j0 + t / w;
+        const int i = 1 + t % w;
+        ks[u] = j * (nx + 1) + i;
+        v[u] = ld(i, j, ks[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+      if (ks[u] >= 0) st(ks[u], v[u]);
+  }
 }
 
 // Calls fn(i, j, k) for every interior node of this CTA's rows.
@@ -196,58 +227,61 @@ struct Solver {
                           const double* dotv) {
     const PLevel& lv = d.lv[l];
     const int pitch = lv.nx + 1;
-    const double wd = d.wd;
+    // z + w/D (b - (8 z - s) / 3) = (1 - 8 w/(3D)) z + w/D b + w/(3D) s:
+    // 7 additions for s, one multiplication and two FMAs.
+    const double wd = d.wd, cz = 1.0 - 8.0 * d.wd / 3.0, cs = d.wd / 3.0;
     double acc = 0.0;
-    for_nodes(lv.nx, lv.ny, part(cluster), [&](int, int, int k) {
-      const double zk = src[k];
-      const double v = zk + wd * (b[k] - (8.0 * zk - nbsum(src, k, pitch)) * (1.0 / 3.0));
-      dst[k] = v;
-      if (dotv) acc = fma(v, dotv[k], acc);
-    });
+    for_nodes_nb<8>(
+        lv.nx, lv.ny, part(cluster),
+        [&](int, int, int k) { return fma(cz, src[k], fma(wd, b[k], cs * nbsum(src, k, pitch))); },
+        [&](int k, double v) {
+          dst[k] = v;
+          if (dotv) acc = fma(v, dotv[k], acc);
+        });
     return acc;
   }
 
-  // The prolongation and correction z = zpre + P zc fused with the first
-  // post-smoothing sweep: the corrected iterate is formed on the fly at the
-  // node and its eight neighbours.
-  __device__ double prolong_sweep(int l, const double* zpre, const double* zc, double* dst,
-                                  const double* b, bool cluster, const double* dotv) {
+  // The prolongation and correction z += P zc of level l, in place
+  // (pointwise: each node reads itself and at most four coarse nodes).
+  __device__ void prolong_add(int l, double* z, const double* zc, bool cluster) {
     const PLevel& lv = d.lv[l];
-    const int pitch = lv.nx + 1, pc = d.lv[l - 1].nx + 1;
-    const double wd = d.wd;
-    double acc = 0.0;
-    for_nodes(lv.nx, lv.ny, part(cluster), [&](int i, int j, int k) {
-      auto zf = [&](int di, int dj) {
-        return zpre[k + dj * pitch + di] + prolong(zc, pc, i + di, j + dj);
-      };
-      const double s = (zf(-1, -1) + zf(0, -1) + zf(1, -1)) + (zf(-1, 0) + zf(1, 0)) +
-                       (zf(-1, 1) + zf(0, 1) + zf(1, 1));
-      const double zk = zf(0, 0);
-      const double v = zk + wd * (b[k] - (8.0 * zk - s) * (1.0 / 3.0));
-      dst[k] = v;
-      if (dotv) acc = fma(v, dotv[k], acc);
-    });
-    return acc;
+    const int pc = d.lv[l - 1].nx + 1;
+    for_nodes_nb<4>(
+        lv.nx, lv.ny, part(cluster),
+        [&](int i, int j, int k) { return z[k] + prolong(zc, pc, i, j); },
+        [&](int k, double v) { z[k] = v; });
   }
 
-  // Full-weighting restriction R = P^T of the residual b - K zpre of level l
-  // (formed on the fly at the nine fine nodes of each coarse node) into the
+  // The residual res = b - K zpre of level l (interior nodes).
+  __device__ void residual(int l, const double* zpre, const double* b, double* res, bool cluster) {
+    const PLevel& lv = d.lv[l];
+    const int pitch = lv.nx + 1;
+    for_nodes_nb<4>(
+        lv.nx, lv.ny, part(cluster),
+        [&](int, int, int k) { return b[k] - (8.0 * zpre[k] - nbsum(zpre, k, pitch)) * (1.0 / 3.0); },
+        [&](int k, double v) { res[k] = v; });
+  }
+
+  // Full-weighting restriction R = P^T of the fine residual res into the
   // right-hand side of level l - 1, and that level's first smoothing step
   // from zero, z = (omega / D) b (pointwise), unless it is the coarsest grid.
-  __device__ void restrict_to(int l, const double* zpre, const double* b, bool cluster) {
+  __device__ void restrict_to(int l, const double* res, bool cluster) {
     const PLevel& f = d.lv[l];
     const PLevel& c = d.lv[l - 1];
     const int pf = f.nx + 1;
     const double wd = d.wd;
     const bool z0 = l - 1 >= 1;
-    for_nodes(c.nx, c.ny, part(cluster), [&](int I, int J, int kc) {
-      const int k = 2 * J * pf + 2 * I;
-      auto res = [&](int kk) { return b[kk] - (8.0 * zpre[kk] - nbsum(zpre, kk, pf)) * (1.0 / 3.0); };
-      const double s = res(k) + 0.5 * ((res(k - 1) + res(k + 1)) + (res(k - pf) + res(k + pf))) +
-                       0.25 * ((res(k - pf - 1) + res(k - pf + 1)) + (res(k + pf - 1) + res(k + pf + 1)));
-      c.b[kc] = s;
-      if (z0) c.z[0][kc] = wd * s;
-    });
+    for_nodes_nb<4>(
+        c.nx, c.ny, part(cluster),
+        [&](int I, int J, int) {
+          const int k = 2 * J * pf + 2 * I;
+          return res[k] + 0.5 * ((res[k - 1] + res[k + 1]) + (res[k - pf] + res[k + pf])) +
+                 0.25 * ((res[k - pf - 1] + res[k - pf + 1]) + (res[k + pf - 1] + res[k + pf + 1]));
+        },
+        [&](int kc, double v) {
+          c.b[kc] = v;
+          if (z0) c.z[0][kc] = wd * v;
+        });
   }
 
   // Coarsest grid: z = K_0^-1 b (one warp per row of the dense inverse).
@@ -265,8 +299,8 @@ struct Solver {
     }
   }
 
-  // Pre-smoothing (the first step from zero is already in z[0]) and the
-  // restriction of level l.
+  // Pre-smoothing (the first step from zero is already in z[0]), the
+  // residual (into the free buffer of the pair) and its restriction, level l.
   __device__ void descend(int l, const double* b, bool cluster) {
     const PLevel& lv = d.lv[l];
     int cur = 0;
@@ -275,21 +309,21 @@ struct Solver {
       cur ^= 1;
       sync(cluster);
     }
-    restrict_to(l, lv.z[cur], b, cluster);
+    residual(l, lv.z[cur], b, lv.z[cur ^ 1], cluster);
+    sync(cluster);
+    restrict_to(l, lv.z[cur ^ 1], cluster);
     sync(cluster);
   }
 
-  // Prolongation, correction and post-smoothing of level l.  With dotv, the
-  // last sweep also forms the partial z . dotv and its barrier is left to
-  // the reduction that follows.
+  // Prolongation and correction, then post-smoothing of level l.  With dotv,
+  // the last sweep also forms the partial z . dotv and its barrier is left
+  // to the reduction that follows.
   __device__ double ascend(int l, const double* b, bool cluster, const double* dotv) {
     const PLevel& lv = d.lv[l];
-    const double* zc = d.lv[l - 1].z[final_buf(l - 1)];
     int cur = pre_buf();
-    double acc = prolong_sweep(l, lv.z[cur], zc, lv.z[cur ^ 1], b, cluster,
-                               d.nu2 == 1 ? dotv : nullptr);
-    cur ^= 1;
-    for (int s = 1; s < d.nu2; ++s) {
+    prolong_add(l, lv.z[cur], d.lv[l - 1].z[final_buf(l - 1)], cluster);
+    double acc = 0.0;
+    for (int s = 0; s < d.nu2; ++s) {
       sync(cluster);
       acc += sweep(l, lv.z[cur], lv.z[cur ^ 1], b, cluster, s == d.nu2 - 1 ? dotv : nullptr);
       cur ^= 1;
@@ -380,14 +414,19 @@ struct Solver {
       }
       const double beta = it == 0 ? 0.0 : rho / rho_old;
       double pq = 0.0;
-      for_nodes(nx, ny, pt, [&](int, int, int k) {
-        const double kz = apply_k(z, k, pitch);
-        const double pk = it == 0 ? z[k] : fma(beta, p[k], z[k]);
-        const double qk = it == 0 ? kz : fma(beta, q[k], kz);
-        p[k] = pk;
-        q[k] = qk;
-        pq = fma(pk, qk, pq);
-      });
+      for_nodes_nb<8>(
+          nx, ny, pt,
+          [&](int, int, int k) {
+            const double kz = apply_k(z, k, pitch);
+            const double pk = it == 0 ? z[k] : fma(beta, p[k], z[k]);
+            const double qk = it == 0 ? kz : fma(beta, q[k], kz);
+            return double2{pk, qk};
+          },
+          [&](int k, double2 v) {
+            p[k] = v.x;
+            q[k] = v.y;
+            pq = fma(v.x, v.y, pq);
+          });
       pq = allreduce1(pq, SLOT_PQ);
       if (!(pq > 0.0) || !isfinite(pq)) {
         status = PST_BREAKDOWN;
@@ -395,13 +434,15 @@ struct Solver {
       }
       const double alpha = rho / pq;
       double rn = 0.0;
-      for_nodes(nx, ny, pt, [&](int, int, int k) {
-        x[k] = fma(alpha, p[k], x[k]);
-        const double rk = fma(-alpha, q[k], r[k]);
-        r[k] = rk;
-        z0[k] = wd * rk;  // the next V-cycle's first smoothing step from zero
-        rn = fma(rk, rk, rn);
-      });
+      for_nodes_nb<8>(
+          nx, ny, pt,
+          [&](int, int, int k) { return double2{fma(alpha, p[k], x[k]), fma(-alpha, q[k], r[k])}; },
+          [&](int k, double2 v) {
+            x[k] = v.x;
+            r[k] = v.y;
+            z0[k] = wd * v.y;  // the next V-cycle's first smoothing step from zero
+            rn = fma(v.y, v.y, rn);
+          });
       rr = allreduce1(rn, SLOT_RR);
       rho_old = rho;
       ++it;
@@ -791,9 +832,11 @@ static mto_status poisson_create_impl(mto_poisson* c, int device, void* stream) 
   PCK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
   PCK(cudaEventCreate(&c->ev_a));
   PCK(cudaEventCreate(&c->ev_b));
-  // Cluster size: one CTA while the finest grid fits one CTA's share of
-  // work, else about one CTA per 4096 interior nodes (a power of two, at
-  // most 16, at most what the device schedules).
+  // Cluster size: one CTA while the finest grid has at most LOCAL_MAX_NODES
+  // interior nodes, else about one CTA per LOCAL_MAX_NODES of them (a power
+  // of two, at most 16, at most what the device schedules): the float64 pipe
+  // of one SM is the bound, so the work is spread as wide as the cluster
+  // allows.
   const long long interior = (long long)(c->nelx - 1) * (c->nely - 1);
   int want = c->o.cluster_ctas;
   if (want == 0) {
