@@ -27,9 +27,14 @@
  * mto_compliance_grad and the diagnostics only enqueue.
  *
  * Threads: a context is not thread-safe; use one context per host thread.
+ *
+ * Profiling: the public calls that do work open an NVTX range named after
+ * the call (mto_set_design, mto_solve, ...).
  */
 #ifndef MTO_H
 #define MTO_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -330,6 +335,17 @@ mto_status mto_set_kernel_timing(mto_ctx* ctx, int enable);
 mto_status mto_measure_fp64_rate(int device, void* cuda_stream, double* ops_per_s);
 mto_status mto_get_kernel_times(mto_ctx* ctx, double* ms_avg, long long* samples);
 mto_status mto_get_launch_count(mto_ctx* ctx, long long* launches);
+
+/* Device memory held by this library (contexts, their load-case workspaces,
+ * batches, Poisson solvers) on all devices, in bytes, and an optional limit
+ * on it (0 = none, the default).  An allocation that would pass the limit
+ * fails as if the device were out of memory -- the call that needed it
+ * returns MTO_ERR_OOM, or runs its load cases one after another when an extra
+ * workspace does not fit -- without calling cudaMalloc.  For hosts that share
+ * the GPU with other allocators, and to exercise the out-of-memory paths.
+ * Thread-safe.  The paper has no counterpart. */
+void mto_set_device_memory_limit(size_t bytes);
+size_t mto_device_memory_in_use(void);
 
 void mto_destroy(mto_ctx* ctx);
 const char* mto_status_string(mto_status s);

@@ -26,8 +26,8 @@ from ._lib import (  # noqa: F401
     SolveStats,
 )
 
-__all__ = ["Mesh", "Batch", "Poisson", "Compliance", "compliance", "measure_fp64_rate", "MtoError",
-           "SolverOpts", "SolveStats"]
+__all__ = ["Mesh", "Batch", "Poisson", "Compliance", "compliance", "measure_fp64_rate",
+           "set_device_memory_limit", "device_memory_in_use", "MtoError", "SolverOpts", "SolveStats"]
 
 
 def _ptr(t):
@@ -44,6 +44,16 @@ def _dev_f64(t, device, name):
     if t.device != device or t.dtype != torch.float64:
         raise ValueError(f"{name} must be a float64 tensor on {device}")
     return t.contiguous()
+
+
+def set_device_memory_limit(nbytes):
+    """Limit on the device memory this library holds (0: none); see include/mto.h."""
+    _lib.load().mto_set_device_memory_limit(int(nbytes))
+
+
+def device_memory_in_use():
+    """Bytes of device memory this library holds now."""
+    return int(_lib.load().mto_device_memory_in_use())
 
 
 def measure_fp64_rate(device=None):

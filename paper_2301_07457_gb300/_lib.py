@@ -137,6 +137,8 @@ SIGNATURES = {
     "mto_poisson_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
     "mto_poisson_destroy": (None, [_P]),
+    "mto_set_device_memory_limit": (None, [ctypes.c_size_t]),
+    "mto_device_memory_in_use": (ctypes.c_size_t, []),
     "mto_destroy": (None, [_P]),
     "mto_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mto_cuda_error_string": (ctypes.c_char_p, []),

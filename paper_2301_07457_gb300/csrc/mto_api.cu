@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -21,11 +23,48 @@ using namespace mto;
 thread_local cudaError_t mto::g_last_cuda = cudaSuccess;
 
 namespace {
+std::mutex g_mem_mutex;
+std::map<void*, size_t> g_mem_blocks;
+size_t g_mem_in_use = 0, g_mem_limit = 0;
+}  // namespace
+
+namespace mto {
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  std::lock_guard<std::mutex> lock(g_mem_mutex);
+  if (g_mem_limit && g_mem_in_use + bytes > g_mem_limit) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  g_mem_blocks[*p] = bytes;
+  g_mem_in_use += bytes;
+  return cudaSuccess;
+}
+
+void device_free(void* p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mutex);
+    auto it = g_mem_blocks.find(p);
+    if (it != g_mem_blocks.end()) {
+      g_mem_in_use -= it->second;
+      g_mem_blocks.erase(it);
+    }
+  }
+  cudaFree(p);
+}
+
+}  // namespace mto
+
+namespace {
 
 mto_status dalloc(mto_ctx* c, void** out, size_t bytes) {
   *out = nullptr;
   if (bytes == 0) bytes = 16;
-  if (cudaMalloc(out, bytes) != cudaSuccess) {
+  if (device_alloc(out, bytes) != cudaSuccess) {
     cudaGetLastError();
     return MTO_ERR_OOM;
   }
@@ -946,6 +985,16 @@ void mto_default_opts(mto_solver_opts* o) {
 
 const char* mto_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }
 
+void mto_set_device_memory_limit(size_t bytes) {
+  std::lock_guard<std::mutex> lock(g_mem_mutex);
+  g_mem_limit = bytes;
+}
+
+size_t mto_device_memory_in_use(void) {
+  std::lock_guard<std::mutex> lock(g_mem_mutex);
+  return g_mem_in_use;
+}
+
 const char* mto_status_string(mto_status s) {
   switch (s) {
     case MTO_OK: return "ok";
@@ -969,7 +1018,7 @@ void mto_destroy(mto_ctx* c) {
   c->slots.clear();
   if (c->ev_slot) cudaEventDestroy(c->ev_slot);
   invalidate_graphs(c);
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) device_free(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->rhs_stats_host) cudaFreeHost(c->rhs_stats_host);
@@ -1127,6 +1176,7 @@ static mto_status create_impl(mto_ctx* c, int nelx, int nely, double nu, unsigne
 
 mto_status mto_create_mesh(mto_ctx** out, int nelx, int nely, double nu, unsigned fixed_edges,
                            const mto_solver_opts* opts, int device, void* cuda_stream) {
+  NvtxRange nvtx_range("mto_create_mesh");
   if (!out) return MTO_ERR_ARG;
   *out = nullptr;
   mto_solver_opts o;
@@ -1158,6 +1208,7 @@ static bool valid_design(int n_phase, const double* E_phase, double penal) {
 
 mto_status mto_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,
                           double penal) {
+  NvtxRange nvtx_range("mto_set_design");
   if (!c || !x_dev || !valid_design(n_phase, E_phase, penal)) return MTO_ERR_ARG;
   ST(enter(c));
   c->has_design = false;
@@ -1168,6 +1219,7 @@ mto_status mto_set_design(mto_ctx* c, int n_phase, const double* x_dev, const do
 
 mto_status mto_solve(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev,
                      mto_solve_stats* stats) {
+  NvtxRange nvtx_range("mto_solve");
   if (!c || n_rhs < 1 || n_rhs > MAX_RHS || !f_dev || !u_dev) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
@@ -1191,6 +1243,7 @@ mto_status mto_last_stats(mto_ctx* c, mto_solve_stats* stats) {
 
 mto_status mto_compliance_grad(mto_ctx* c, int n_rhs, const double* f_dev, const double* u_dev,
                                double* compliance_dev, double* dcdx_dev) {
+  NvtxRange nvtx_range("mto_compliance_grad");
   if (!c || n_rhs < 1 || !f_dev || !u_dev || !compliance_dev) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
@@ -1201,6 +1254,7 @@ mto_status mto_compliance_grad(mto_ctx* c, int n_rhs, const double* f_dev, const
 mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const double* E_phase,
                         double penal, int n_rhs, const double* f_host, double* u_host,
                         double* compliance_host, double* dcdx_host, mto_solve_stats* stats) {
+  NvtxRange nvtx_range("mto_run_host");
   if (!c || !x_host || n_rhs < 1 || n_rhs > MAX_RHS || !f_host || !u_host || !compliance_host ||
       !valid_design(n_phase, E_phase, penal))
     return MTO_ERR_ARG;

@@ -55,7 +55,7 @@ mto_status grow_design(mto_ctx* c, int n_phase) {
   const size_t need = (size_t)n_phase * c->nelx * c->nely;
   if (c->xdes_cap >= need) return MTO_OK;
   void* p = nullptr;
-  if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) {
+  if (device_alloc(&p, need * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return MTO_ERR_OOM;
   }
@@ -112,6 +112,7 @@ extern "C" {
 
 mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const mto_batch_item* items,
                             void* cuda_stream) {
+  NvtxRange nvtx_range("mto_batch_create");
   if (!out || n < 1 || !ctxs || !items) return MTO_ERR_ARG;
   *out = nullptr;
   const int device = ctxs[0] ? ctxs[0]->device : -1;
@@ -211,6 +212,7 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
 }
 
 mto_status mto_batch_run(mto_batch* b, mto_solve_stats* stats) {
+  NvtxRange nvtx_range("mto_batch_run");
   if (!b) return MTO_ERR_ARG;
   CK(cudaSetDevice(b->device));
   CK(cudaEventRecord(b->ev_in, b->user_stream));
@@ -332,6 +334,7 @@ static mto_status tune_one(mto_ctx* c, const std::tuple<int, int, int, int, int>
 }
 
 extern "C" mto_status mto_autotune(mto_ctx* c) {
+  NvtxRange nvtx_range("mto_autotune");
   if (!c) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   CK(cudaSetDevice(c->device));

@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mto.h"
 #include "mto_launch.h"
 
@@ -159,6 +161,21 @@ extern thread_local cudaError_t g_last_cuda;
     mto_status s_ = (call);               \
     if (s_ != MTO_OK) return s_;          \
   } while (0)
+
+// Device memory of the library: every allocation goes through these, which
+// keep a process-wide count of the bytes held and refuse an allocation that
+// would pass the limit set by mto_set_device_memory_limit (0: none) with
+// cudaErrorMemoryAllocation, without calling cudaMalloc.
+cudaError_t device_alloc(void** p, size_t bytes);
+void device_free(void* p);
+
+// An NVTX range around a public call (no cost without a profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Shared by the translation units (defined in mto_api.cu).
 mto_status enqueue_set_design(mto_ctx* c, int n_phase, const double* x_dev, const double* E_phase,

@@ -658,36 +658,36 @@ mto_status grow_ws(mto_poisson* c, int n_rhs) {
   if (n_rhs <= c->cap) return MTO_OK;
   const WsLayout w = ws_layout(c);
   double* ws = nullptr;
-  if (cudaMalloc(&ws, sizeof(double) * w.total * n_rhs) != cudaSuccess) {
+  if (mto::device_alloc((void**)&ws, sizeof(double) * w.total * n_rhs) != cudaSuccess) {
     cudaGetLastError();
     return MTO_ERR_OOM;
   }
   // Boundary entries are never written by the kernel: zero them once.
   if (cudaMemset(ws, 0, sizeof(double) * w.total * n_rhs) != cudaSuccess) {
-    cudaFree(ws);
+    mto::device_free(ws);
     return fail_cuda(cudaGetLastError());
   }
   PDesc* dd = nullptr;
   PStats* ds = nullptr;
-  if (cudaMalloc(&dd, sizeof(PDesc) * n_rhs) != cudaSuccess ||
-      cudaMalloc(&ds, sizeof(PStats) * n_rhs) != cudaSuccess) {
+  if (mto::device_alloc((void**)&dd, sizeof(PDesc) * n_rhs) != cudaSuccess ||
+      mto::device_alloc((void**)&ds, sizeof(PStats) * n_rhs) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(ws);
-    if (dd) cudaFree(dd);
+    mto::device_free(ws);
+    if (dd) mto::device_free(dd);
     return MTO_ERR_OOM;
   }
   PStats* hs = nullptr;
   if (cudaMallocHost(&hs, sizeof(PStats) * n_rhs) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(ws);
-    cudaFree(dd);
-    cudaFree(ds);
+    mto::device_free(ws);
+    mto::device_free(dd);
+    mto::device_free(ds);
     return MTO_ERR_OOM;
   }
   cudaStreamSynchronize(c->stream);
-  if (c->ws) cudaFree(c->ws);
-  if (c->d_desc) cudaFree(c->d_desc);
-  if (c->d_stats) cudaFree(c->d_stats);
+  if (c->ws) mto::device_free(c->ws);
+  if (c->d_desc) mto::device_free(c->d_desc);
+  if (c->d_stats) mto::device_free(c->d_stats);
   if (c->h_stats) cudaFreeHost(c->h_stats);
   c->ws = ws;
   c->d_desc = dd;
@@ -810,13 +810,13 @@ void mto_poisson_destroy(mto_poisson* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->ws) cudaFree(c->ws);
-  if (c->d_desc) cudaFree(c->d_desc);
-  if (c->d_stats) cudaFree(c->d_stats);
+  if (c->ws) mto::device_free(c->ws);
+  if (c->d_desc) mto::device_free(c->d_desc);
+  if (c->d_stats) mto::device_free(c->d_stats);
   if (c->h_stats) cudaFreeHost(c->h_stats);
-  if (c->Kinv) cudaFree(c->Kinv);
-  if (c->Ab) cudaFree(c->Ab);
-  if (c->err) cudaFree(c->err);
+  if (c->Kinv) mto::device_free(c->Kinv);
+  if (c->Ab) mto::device_free(c->Ab);
+  if (c->err) mto::device_free(c->err);
   for (cudaEvent_t e : {c->ev_in, c->ev_out, c->ev_a, c->ev_b})
     if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -862,9 +862,9 @@ static mto_status poisson_create_impl(mto_poisson* c, int device, void* stream) 
   const int nx0 = c->nelx >> c->L, ny0 = c->nely >> c->L;
   c->n0 = (nx0 - 1) * (ny0 - 1);
   const int ld = nx0 + 1;  // band width + 1
-  if (cudaMalloc(&c->Kinv, sizeof(double) * (size_t)c->n0 * c->n0) != cudaSuccess ||
-      cudaMalloc(&c->Ab, sizeof(double) * (size_t)c->n0 * ld) != cudaSuccess ||
-      cudaMalloc(&c->err, sizeof(int)) != cudaSuccess) {
+  if (mto::device_alloc((void**)&c->Kinv, sizeof(double) * (size_t)c->n0 * c->n0) != cudaSuccess ||
+      mto::device_alloc((void**)&c->Ab, sizeof(double) * (size_t)c->n0 * ld) != cudaSuccess ||
+      mto::device_alloc((void**)&c->err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return MTO_ERR_OOM;
   }
@@ -884,6 +884,7 @@ static mto_status poisson_create_impl(mto_poisson* c, int device, void* stream) 
 
 mto_status mto_poisson_create(mto_poisson** out, int nelx, int nely, const mto_poisson_opts* opts,
                               int device, void* cuda_stream) {
+  mto::NvtxRange nvtx_range("mto_poisson_create");
   if (!out) return MTO_ERR_ARG;
   *out = nullptr;
   mto_poisson_opts o;
@@ -918,6 +919,7 @@ mto_status mto_poisson_create(mto_poisson** out, int nelx, int nely, const mto_p
 
 mto_status mto_poisson_solve(mto_poisson* c, int n_rhs, const double* f_dev, double* u_dev,
                              mto_solve_stats* stats) {
+  mto::NvtxRange nvtx_range("mto_poisson_solve");
   if (!c || !f_dev || !u_dev || n_rhs < 1 || n_rhs > PMAX_RHS) return MTO_ERR_ARG;
   mto_status s = enter(c);
   if (s != MTO_OK) return s;

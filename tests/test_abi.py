@@ -94,3 +94,11 @@ def test_poisson_argument_validation_needs_no_gpu(libpath):
     assert create(64, 64) == _lib.ERR_ARG
     assert lib.mto_poisson_solve(None, 1, None, None, None) == _lib.ERR_ARG
     assert lib.mto_poisson_create(None, 8, 8, None, 0, None) == _lib.ERR_ARG
+
+
+def test_memory_ledger_needs_no_gpu(libpath):
+    from paper_2301_07457_gb300 import _lib
+    lib = _lib.load()
+    assert lib.mto_device_memory_in_use() == 0  # nothing allocated in this process
+    lib.mto_set_device_memory_limit(1 << 20)
+    lib.mto_set_device_memory_limit(0)
