@@ -173,9 +173,16 @@ mto_status mto_solve_batched(int n, mto_ctx* const* ctxs, const mto_batch_item* 
  * synchronises; later solves and batches use the chosen shapes.
  * mto_get_launch_shape returns the chosen warps per launch, or 0 for the
  * default: one full wave of the sweep kernel (its resident blocks per SM,
- * set by its register use, times the SM count). */
+ * set by its register use, times the SM count); level -1 is the float64
+ * outer sweeps. */
 mto_status mto_autotune(mto_ctx* ctx);
 mto_status mto_get_launch_shape(mto_ctx* ctx, int level, int* target_warps);
+/* Sets the warps per launch of level's sweeps by hand (0: one full wave);
+ * level -1 addresses the float64 outer sweeps of the finest level (K p and
+ * the residuals), 0..n_coarsen the V-cycle sweeps.  target_warps <= 128 per
+ * SM.  The solver's graphs are rebuilt on the next solve; results do not
+ * depend on the shape beyond the order of the reductions' partial sums. */
+mto_status mto_set_launch_shape(mto_ctx* ctx, int level, int target_warps);
 
 /* Statistics of the last mto_solve (synchronises the context's stream). */
 mto_status mto_last_stats(mto_ctx* ctx, mto_solve_stats* stats);

@@ -228,6 +228,11 @@ class Mesh:
         _lib.check(self._lib.mto_get_launch_shape(self._h, level, ctypes.byref(t)), "mto_get_launch_shape")
         return t.value
 
+    def set_launch_shape(self, level, target_warps):
+        """Warps per launch of a level's sweeps (0: one full wave; level -1: the
+        float64 outer sweeps)."""
+        _lib.check(self._lib.mto_set_launch_shape(self._h, level, int(target_warps)), "mto_set_launch_shape")
+
     def set_kernel_timing(self, enable):
         _lib.check(self._lib.mto_set_kernel_timing(self._h, int(enable)), "mto_set_kernel_timing")
 

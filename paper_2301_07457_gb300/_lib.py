@@ -124,6 +124,7 @@ SIGNATURES = {
                                          ctypes.POINTER(SolveStats), _P]),
     "mto_autotune": (ctypes.c_int, [_P]),
     "mto_get_launch_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mto_set_launch_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "mto_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "mto_get_kernel_times": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
     "mto_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),

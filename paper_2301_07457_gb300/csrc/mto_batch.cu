@@ -409,8 +409,18 @@ extern "C" mto_status mto_autotune(mto_ctx* c) {
 extern "C" {
 
 mto_status mto_get_launch_shape(mto_ctx* c, int level, int* target_warps_out) {
-  if (!c || !target_warps_out || level < 0 || level > c->L) return MTO_ERR_ARG;
-  *target_warps_out = target_warps(c, level);
+  if (!c || !target_warps_out || level < -1 || level > c->L) return MTO_ERR_ARG;
+  *target_warps_out = level < 0 ? target_warps64(c) : target_warps(c, level);
+  return MTO_OK;
+}
+
+mto_status mto_set_launch_shape(mto_ctx* c, int level, int target_warps) {
+  if (!c || level < -1 || level > c->L || target_warps < 0 ||
+      target_warps > MAX_TARGET_WARPS_PER_SM * c->num_sms)
+    return MTO_ERR_ARG;
+  if (level < 0) c->tw64 = target_warps;
+  else c->tw[level] = target_warps;
+  invalidate_graphs(c);
   return MTO_OK;
 }
 
