@@ -265,7 +265,8 @@ mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu, int n_phas
  * inverse factored with Alg. 3).  One DOF per node; nodal vectors are
  * [nely+1][nelx+1] float64.  The constant-coefficient Q4 Laplacian is the
  * 9-point stencil (8 u_n - sum of the 8 neighbours) / 3 on every grid (its
- * Galerkin coarse operator is the same stencil).  Float64 throughout.
+ * Galerkin coarse operator is the same stencil).  Float64 throughout, or
+ * a float32 V-cycle inside the float64 CG (precision MIXED).
  *
  * A solve is ONE kernel launch: each right-hand side is solved by one
  * thread-block cluster (cluster_ctas CTAs; 0 = chosen by mesh size, one CTA
@@ -283,10 +284,13 @@ typedef struct {
   int cluster_ctas;  /* 0 (automatic), 1, 2, 4, 8 or 16 CTAs per right-hand side; more than
                         one only when the finest grid has over 256 interior nodes, and at
                         most what the device can schedule */
+  int precision;     /* MTO_PRECISION_FP64, or MTO_PRECISION_MIXED: the V-cycle (smoothing,
+                        transfers, coarse grids) in float32, the CG vectors, K p, dot
+                        products and the coarsest dense solve in float64, flexible beta */
 } mto_poisson_opts;
 
 /* Defaults: tol 1e-8, max_it 500, omega 0.6, nu1 = nu2 = 2, n_coarsen 3,
- * cluster_ctas 0. */
+ * cluster_ctas 0, precision FP64. */
 void mto_poisson_default_opts(mto_poisson_opts* opts);
 
 /* Creates the solver for an nelx x nely mesh (both >= 2, divisible by

@@ -326,17 +326,18 @@ class Batch:
 class Poisson:
     """The scalar Poisson problem of Sec. 5.1 (-Laplace u = f, u = 0 on the
     boundary, nelx x nely unit Q4 elements) solved by pCGMG in one cluster
-    kernel launch per solve.  Nodal vectors are float64 [ny+1][nx+1] (or
+    kernel launch per solve; precision "fp64" or "mixed" (float32 V-cycle).  Nodal vectors are float64 [ny+1][nx+1] (or
     [n_rhs][ny+1][nx+1]) on the device."""
 
     def __init__(self, nelx, nely, n_coarsen=3, tol=1e-8, max_it=500, omega=0.6, nu1=2, nu2=2,
-                 cluster_ctas=0, device=None):
+                 cluster_ctas=0, precision="fp64", device=None):
         lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         o = _lib.PoissonOpts()
         lib.mto_poisson_default_opts(ctypes.byref(o))
         o.tol, o.max_it, o.omega, o.nu1, o.nu2 = tol, max_it, omega, nu1, nu2
         o.n_coarsen, o.cluster_ctas = n_coarsen, cluster_ctas
+        o.precision = {"fp64": PRECISION_FP64, "mixed": PRECISION_MIXED}[precision]
         self.opts, self.nelx, self.nely, self._lib = o, nelx, nely, lib
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -71,6 +71,7 @@ class PoissonOpts(ctypes.Structure):
         ("nu2", ctypes.c_int),
         ("n_coarsen", ctypes.c_int),
         ("cluster_ctas", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 

@@ -46,8 +46,8 @@ enum { PST_RUNNING = 0, PST_CONVERGED = 1, PST_MAXIT = 2, PST_BREAKDOWN = 3 };
 
 struct PLevel {
   int nx, ny;       // elements; nodes (nx + 1) x (ny + 1), row pitch nx + 1
-  double* z[2];     // iterates (ping-pong); boundary entries stay zero
-  double* b;        // right-hand side (coarse levels)
+  void* z[2];       // iterates (ping-pong) in the V-cycle's type; boundary entries stay zero
+  void* b;          // right-hand side (coarse levels), same type
 };
 
 struct PStats {
@@ -57,7 +57,7 @@ struct PStats {
 
 struct PDesc {
   int L, fl;                 // finest level; levels 0..fl run on CTA 0 alone
-  int mode, nu1, nu2, max_it;
+  int mode, nu1, nu2, max_it, flexible;
   double tol2, wd;           // tol^2, omega / D = 3 omega / 8
   int n0;                    // interior nodes of the coarsest grid
   const double* Kinv;        // n0 x n0, row-major
@@ -71,25 +71,6 @@ struct PDesc {
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double nbsum(const double* z, int k, int pitch) {
-  return (z[k - pitch - 1] + z[k - pitch] + z[k - pitch + 1]) + (z[k - 1] + z[k + 1]) +
-         (z[k + pitch - 1] + z[k + pitch] + z[k + pitch + 1]);
-}
-
-// (K z)(k) for the 9-point Q4 stencil.
-__device__ __forceinline__ double apply_k(const double* z, int k, int pitch) {
-  return (8.0 * z[k] - nbsum(z, k, pitch)) * (1.0 / 3.0);
-}
-
-// Bilinear interpolation of the coarse vector zc (pitch pc) at fine node (i, j).
-__device__ __forceinline__ double prolong(const double* zc, int pc, int i, int j) {
-  const int I = i >> 1, J = j >> 1;
-  const int k = J * pc + I;
-  if (!(j & 1)) return (i & 1) ? 0.5 * (zc[k] + zc[k + 1]) : zc[k];
-  if (!(i & 1)) return 0.5 * (zc[k] + zc[k + pc]);
-  return 0.25 * ((zc[k] + zc[k + 1]) + (zc[k + pc] + zc[k + pc + 1]));
-}
-
 // Work split of a phase: this CTA's block of interior node rows [j0, j1) of a
 // level with ny elements in y, and its rank / size (1 for CTA-local phases).
 struct Part {
@@ -152,27 +133,51 @@ template <typename F> __device__ __forceinline__ void for_nodes(int nx, int ny, 
 namespace {
 
 struct PShared {
-  double red[4][PMAXC];   // all-gathered partial sums, one row per reduction slot
+  double red[5][PMAXC];   // all-gathered partial sums, one row per reduction slot
   double warp[2][PWARPS];
 };
 
 // Reduction slots (each used once per PCG iteration, so that consecutive
 // uses of a slot are separated by several barriers).
-enum { SLOT_RHO = 0, SLOT_PQ = 1, SLOT_RR = 2, SLOT_FF = 3, SLOT_TRUE = 3 };
+enum { SLOT_RHO = 0, SLOT_PQ = 1, SLOT_RR = 2, SLOT_FF = 3, SLOT_TRUE = 3, SLOT_ZQ = 4 };
 
-struct Solver {
+// The 9-point stencil on a vector of type T, evaluated in float64.
+template <typename T> __device__ __forceinline__ double apply_k64(const T* z, int k, int pitch) {
+  auto v = [&](int o) { return (double)z[k + o]; };
+  const double s = (v(-pitch - 1) + v(-pitch) + v(-pitch + 1)) + (v(-1) + v(1)) +
+                   (v(pitch - 1) + v(pitch) + v(pitch + 1));
+  return (8.0 * v(0) - s) * (1.0 / 3.0);
+}
+
+template <typename T> __device__ __forceinline__ T nbsum_t(const T* z, int k, int pitch) {
+  return (z[k - pitch - 1] + z[k - pitch] + z[k - pitch + 1]) + (z[k - 1] + z[k + 1]) +
+         (z[k + pitch - 1] + z[k + pitch] + z[k + pitch + 1]);
+}
+
+template <typename T> __device__ __forceinline__ T prolong_t(const T* zc, int pc, int i, int j) {
+  const int I = i >> 1, J = j >> 1;
+  const int k = J * pc + I;
+  const T h = T(0.5), qt = T(0.25);
+  if (!(j & 1)) return (i & 1) ? h * (zc[k] + zc[k + 1]) : zc[k];
+  if (!(i & 1)) return h * (zc[k] + zc[k + pc]);
+  return qt * ((zc[k] + zc[k + 1]) + (zc[k + pc] + zc[k + pc + 1]));
+}
+
+// The V-cycle runs in VT (double, or float for the mixed precision); the
+// CG vectors, dot products and the stopping test are float64 in both.
+template <typename VT> struct Solver {
   const PDesc& d;
   PShared& sh;
   int rank, C;
   cg::cluster_group cl;
 
   __device__ Part part(bool cluster) const { return cluster ? Part{rank, C} : Part{0, 1}; }
-  // Level l is split over the cluster (else it runs in CTA 0 alone).
-  __device__ bool split(int l) const { return C > 1 && l > d.fl; }
   __device__ void sync(bool cluster) {
     if (cluster) cl.sync();
     else __syncthreads();
   }
+  __device__ VT* Z(int l, int i) const { return static_cast<VT*>(d.lv[l].z[i]); }
+  __device__ VT* B(int l) const { return static_cast<VT*>(d.lv[l].b); }
   // Iterate buffers: the pre-smoothed iterate and the final one of level l.
   __device__ int pre_buf() const { return (d.nu1 - 1) & 1; }
   __device__ int final_buf(int l) const { return l == 0 ? 0 : (d.nu1 - 1 + d.nu2) & 1; }
@@ -221,144 +226,168 @@ struct Solver {
     return a;
   }
 
-  // dst = src + (omega / D)(b - K src) on level l; returns the sum of
-  // dst * dotv over this CTA's nodes (dotv may be null).
-  __device__ double sweep(int l, const double* src, double* dst, const double* b, bool cluster,
-                          const double* dotv) {
+  // dst = src + (omega / D)(b - K src) on level l, in VT:
+  // (1 - 8 w/(3D)) z + w/D b + w/(3D) s with s the sum of the 8 neighbours
+  // (7 additions, one multiplication, two FMAs).  With dotv (and dotq) the
+  // float64 sums dst . dotv (dst . dotq) over this CTA's nodes are added to
+  // acc (accq).
+  template <typename BT>
+  __device__ void sweep(int l, const VT* src, VT* dst, const BT* b, bool cluster, const double* dotv,
+                        const double* dotq, double& acc, double& accq) {
     const PLevel& lv = d.lv[l];
     const int pitch = lv.nx + 1;
-    // z + w/D (b - (8 z - s) / 3) = (1 - 8 w/(3D)) z + w/D b + w/(3D) s:
-    // 7 additions for s, one multiplication and two FMAs.
-    const double wd = d.wd, cz = 1.0 - 8.0 * d.wd / 3.0, cs = d.wd / 3.0;
-    double acc = 0.0;
-    for_nodes_nb<8>(
+    const VT wd = VT(d.wd), cz = VT(1.0 - 8.0 * d.wd / 3.0), cs = VT(d.wd / 3.0);
+    // Nodes in flight per thread: as many as the 255-register budget holds.
+    constexpr int NB = sizeof(VT) == 8 ? 4 : 8;
+    for_nodes_nb<NB>(
         lv.nx, lv.ny, part(cluster),
-        [&](int, int, int k) { return fma(cz, src[k], fma(wd, b[k], cs * nbsum(src, k, pitch))); },
-        [&](int k, double v) {
+        [&](int, int, int k) {
+          return fma(cz, src[k], fma(wd, VT(b[k]), cs * nbsum_t(src, k, pitch)));
+        },
+        [&](int k, VT v) {
           dst[k] = v;
-          if (dotv) acc = fma(v, dotv[k], acc);
+          if (dotv) acc = fma((double)v, dotv[k], acc);
+          if (dotq) accq = fma((double)v, dotq[k], accq);
         });
-    return acc;
   }
 
   // The prolongation and correction z += P zc of level l, in place
   // (pointwise: each node reads itself and at most four coarse nodes).
-  __device__ void prolong_add(int l, double* z, const double* zc, bool cluster) {
+  __device__ void prolong_add(int l, VT* z, const VT* zc, bool cluster) {
     const PLevel& lv = d.lv[l];
     const int pc = d.lv[l - 1].nx + 1;
     for_nodes_nb<4>(
         lv.nx, lv.ny, part(cluster),
-        [&](int i, int j, int k) { return z[k] + prolong(zc, pc, i, j); },
-        [&](int k, double v) { z[k] = v; });
+        [&](int i, int j, int k) { return z[k] + prolong_t(zc, pc, i, j); },
+        [&](int k, VT v) { z[k] = v; });
   }
 
-  // The residual res = b - K zpre of level l (interior nodes).
-  __device__ void residual(int l, const double* zpre, const double* b, double* res, bool cluster) {
+  // The residual res = b - K zpre of level l (interior nodes), in VT.
+  template <typename BT>
+  __device__ void residual(int l, const VT* zpre, const BT* b, VT* res, bool cluster) {
     const PLevel& lv = d.lv[l];
     const int pitch = lv.nx + 1;
+    const VT third = VT(1.0 / 3.0);
     for_nodes_nb<4>(
         lv.nx, lv.ny, part(cluster),
-        [&](int, int, int k) { return b[k] - (8.0 * zpre[k] - nbsum(zpre, k, pitch)) * (1.0 / 3.0); },
-        [&](int k, double v) { res[k] = v; });
+        [&](int, int, int k) { return VT(b[k]) - (VT(8) * zpre[k] - nbsum_t(zpre, k, pitch)) * third; },
+        [&](int k, VT v) { res[k] = v; });
   }
 
   // Full-weighting restriction R = P^T of the fine residual res into the
   // right-hand side of level l - 1, and that level's first smoothing step
   // from zero, z = (omega / D) b (pointwise), unless it is the coarsest grid.
-  __device__ void restrict_to(int l, const double* res, bool cluster) {
-    const PLevel& f = d.lv[l];
+  __device__ void restrict_to(int l, const VT* res, bool cluster) {
+    const int pf = d.lv[l].nx + 1;
     const PLevel& c = d.lv[l - 1];
-    const int pf = f.nx + 1;
-    const double wd = d.wd;
-    const bool z0 = l - 1 >= 1;
+    VT* bc = B(l - 1);
+    VT* z0 = Z(l - 1, 0);
+    const VT wd = VT(d.wd), h = VT(0.5), qt = VT(0.25);
+    const bool first = l - 1 >= 1;
     for_nodes_nb<4>(
         c.nx, c.ny, part(cluster),
         [&](int I, int J, int) {
           const int k = 2 * J * pf + 2 * I;
-          return res[k] + 0.5 * ((res[k - 1] + res[k + 1]) + (res[k - pf] + res[k + pf])) +
-                 0.25 * ((res[k - pf - 1] + res[k - pf + 1]) + (res[k + pf - 1] + res[k + pf + 1]));
+          return res[k] + h * ((res[k - 1] + res[k + 1]) + (res[k - pf] + res[k + pf])) +
+                 qt * ((res[k - pf - 1] + res[k - pf + 1]) + (res[k + pf - 1] + res[k + pf + 1]));
         },
-        [&](int kc, double v) {
-          c.b[kc] = v;
-          if (z0) c.z[0][kc] = wd * v;
+        [&](int kc, VT v) {
+          bc[kc] = v;
+          if (first) z0[kc] = wd * v;
         });
   }
 
-  // Coarsest grid: z = K_0^-1 b (one warp per row of the dense inverse).
+  // Coarsest grid: z = K_0^-1 b (float64 dense inverse, one warp per row).
   __device__ void coarsest() {
     const PLevel& c = d.lv[0];
+    const VT* b0 = B(0);
+    VT* z0 = Z(0, 0);
     const int n = d.n0, w = c.nx - 1, pitch = c.nx + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int a = warp; a < n; a += PWARPS) {
       double s = 0.0;
       for (int bb = lane; bb < n; bb += 32)
-        s = fma(d.Kinv[(size_t)a * n + bb], c.b[(1 + bb / w) * pitch + 1 + bb % w], s);
+        s = fma(d.Kinv[(size_t)a * n + bb], (double)b0[(1 + bb / w) * pitch + 1 + bb % w], s);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) c.z[0][(1 + a / w) * pitch + 1 + a % w] = s;
+      if (lane == 0) z0[(1 + a / w) * pitch + 1 + a % w] = VT(s);
     }
   }
 
   // Pre-smoothing (the first step from zero is already in z[0]), the
   // residual (into the free buffer of the pair) and its restriction, level l.
-  __device__ void descend(int l, const double* b, bool cluster) {
-    const PLevel& lv = d.lv[l];
+  template <typename BT> __device__ void descend(int l, const BT* b, bool cluster) {
     int cur = 0;
+    double u = 0.0, v = 0.0;
     for (int s = 1; s < d.nu1; ++s) {
-      sweep(l, lv.z[cur], lv.z[cur ^ 1], b, cluster, nullptr);
+      sweep(l, Z(l, cur), Z(l, cur ^ 1), b, cluster, nullptr, nullptr, u, v);
       cur ^= 1;
       sync(cluster);
     }
-    residual(l, lv.z[cur], b, lv.z[cur ^ 1], cluster);
+    residual(l, Z(l, cur), b, Z(l, cur ^ 1), cluster);
     sync(cluster);
-    restrict_to(l, lv.z[cur ^ 1], cluster);
+    restrict_to(l, Z(l, cur ^ 1), cluster);
     sync(cluster);
   }
 
   // Prolongation and correction, then post-smoothing of level l.  With dotv,
-  // the last sweep also forms the partial z . dotv and its barrier is left
-  // to the reduction that follows.
-  __device__ double ascend(int l, const double* b, bool cluster, const double* dotv) {
-    const PLevel& lv = d.lv[l];
+  // the last sweep also forms the partial sums z . dotv (and z . dotq) and
+  // its barrier is left to the reduction that follows.
+  template <typename BT>
+  __device__ void ascend(int l, const BT* b, bool cluster, const double* dotv, const double* dotq,
+                         double& acc, double& accq) {
     int cur = pre_buf();
-    prolong_add(l, lv.z[cur], d.lv[l - 1].z[final_buf(l - 1)], cluster);
-    double acc = 0.0;
+    prolong_add(l, Z(l, cur), Z(l - 1, final_buf(l - 1)), cluster);
     for (int s = 0; s < d.nu2; ++s) {
       sync(cluster);
-      acc += sweep(l, lv.z[cur], lv.z[cur ^ 1], b, cluster, s == d.nu2 - 1 ? dotv : nullptr);
+      const bool last = s == d.nu2 - 1;
+      sweep(l, Z(l, cur), Z(l, cur ^ 1), b, cluster, last ? dotv : nullptr, last ? dotq : nullptr, acc,
+            accq);
       cur ^= 1;
     }
     if (!dotv) sync(cluster);
-    return acc;
   }
 
-  // One V-cycle (Alg. 1 with gamma = 1) for the finest right-hand side bL,
-  // whose first smoothing step is already in lv[L].z[0].  Returns this CTA's
-  // part of z . dotv when dotv is given (the caller reduces it).
-  __device__ double vcycle(const double* bL, const double* dotv) {
+  // One V-cycle (Alg. 1 with gamma = 1) for the finest right-hand side bL
+  // (float64), whose first smoothing step is already in Z(L, 0).  With dotv
+  // (dotq), this CTA's part of z . dotv (z . dotq) is added to acc (accq);
+  // the caller reduces them.
+  __device__ void vcycle(const double* bL, const double* dotv, const double* dotq, double& acc,
+                         double& accq) {
     const int L = d.L;
     const int top_local = C > 1 ? d.fl : L;
-    for (int l = L; l > top_local; --l) descend(l, l == L ? bL : d.lv[l].b, true);
-    double acc = 0.0;
+    for (int l = L; l > top_local; --l) {
+      if (l == L) descend(l, bL, true);
+      else descend(l, static_cast<const VT*>(B(l)), true);
+    }
     if (C == 1 || rank == 0) {
-      for (int l = top_local; l >= 1; --l) descend(l, l == L ? bL : d.lv[l].b, false);
+      for (int l = top_local; l >= 1; --l) {
+        if (l == L) descend(l, bL, false);
+        else descend(l, static_cast<const VT*>(B(l)), false);
+      }
       coarsest();
       __syncthreads();
-      for (int l = 1; l <= top_local; ++l)
-        acc += ascend(l, l == L ? bL : d.lv[l].b, false, l == L ? dotv : nullptr);
+      for (int l = 1; l <= top_local; ++l) {
+        if (l == L) ascend(l, bL, false, dotv, dotq, acc, accq);
+        else ascend(l, static_cast<const VT*>(B(l)), false, nullptr, nullptr, acc, accq);
+      }
     }
     if (C > 1) cl.sync();
-    for (int l = top_local + 1; l <= L; ++l)
-      acc += ascend(l, l == L ? bL : d.lv[l].b, true, l == L ? dotv : nullptr);
-    return acc;
+    for (int l = top_local + 1; l <= L; ++l) {
+      if (l == L) ascend(l, bL, true, dotv, dotq, acc, accq);
+      else ascend(l, static_cast<const VT*>(B(l)), true, nullptr, nullptr, acc, accq);
+    }
   }
 
   // ------------------------------------------------------------------------
-  // Alg. 2 with the V-cycle above as preconditioner, Fletcher-Reeves beta;
-  // stop when ||r|| <= tol ||f|| (tested before the preconditioner).
-  // q = K p is formed as K z + beta q (K is linear), so that the phase needs
-  // z at the neighbours (complete after the V-cycle's last barrier) but p
-  // only at the node itself.
+  // Alg. 2 with the V-cycle above as preconditioner; stop when
+  // ||r|| <= tol ||f|| (tested before the preconditioner).  beta is
+  // Fletcher-Reeves (float64 V-cycle) or the flexible form
+  // z_i . (r_i - r_{i-1}) / rho_{i-1} = -alpha_{i-1} z_i . q_{i-1} / rho_{i-1}
+  // (float32 V-cycle), with z . q formed in the last smoothing sweep.
+  // q = K p is formed as K z + beta q (K is linear, evaluated in float64), so
+  // that the phase needs z at the neighbours (complete after the V-cycle's
+  // last barrier) but p only at the node itself.
   // ------------------------------------------------------------------------
   __device__ void solve() {
     const PLevel& F = d.lv[d.L];
@@ -368,7 +397,7 @@ struct Solver {
     double* x = d.x;
     double *r = d.r, *p = d.p, *q = d.q;
     const double* f = d.f;
-    double* z0 = F.z[0];
+    VT* z0 = Z(d.L, 0);
     const double wd = d.wd;
     // Warm start: the iterate is zero on the boundary.
     if (rank == 0) {
@@ -384,16 +413,17 @@ struct Solver {
     sync(cl_on);
     double rr = 0.0, ff = 0.0;
     for_nodes(nx, ny, pt, [&](int, int, int k) {
-      const double rk = f[k] - apply_k(x, k, pitch);
+      const double rk = f[k] - apply_k64(x, k, pitch);
       r[k] = rk;
-      z0[k] = wd * rk;
+      z0[k] = VT(wd * rk);
       rr = fma(rk, rk, rr);
       ff = fma(f[k], f[k], ff);
     });
     allreduce(rr, ff, SLOT_RR, SLOT_FF);
     int it = 0, status = PST_RUNNING;
-    double rho_old = 1.0;
-    const double* z = F.z[final_buf(d.L)];
+    double rho_old = 1.0, alpha_old = 0.0;
+    const VT* z = Z(d.L, final_buf(d.L));
+    constexpr int NBC = sizeof(VT) == 8 ? 4 : 8;  // nodes in flight per thread (registers)
     for (;;) {
       if (!isfinite(rr)) {
         status = PST_BREAKDOWN;
@@ -407,18 +437,31 @@ struct Solver {
         status = PST_MAXIT;
         break;
       }
-      const double rho = allreduce1(vcycle(r, r), SLOT_RHO);
+      // The flexible form belongs to the float32 V-cycle (compiled out of
+      // the float64 one).
+      constexpr bool FLEX = sizeof(VT) == 4;
+      const bool flex = FLEX && d.flexible && it > 0;
+      double rho = 0.0, zq = 0.0;
+      if constexpr (FLEX) {
+        vcycle(r, r, flex ? q : nullptr, rho, zq);
+        if (flex) allreduce(rho, zq, SLOT_RHO, SLOT_ZQ);
+        else rho = allreduce1(rho, SLOT_RHO);
+      } else {
+        vcycle(r, r, nullptr, rho, zq);
+        rho = allreduce1(rho, SLOT_RHO);
+      }
       if (!(rho > 0.0) || !isfinite(rho)) {
         status = PST_BREAKDOWN;
         break;
       }
-      const double beta = it == 0 ? 0.0 : rho / rho_old;
+      const double beta = it == 0 ? 0.0 : (flex ? -alpha_old * zq / rho_old : rho / rho_old);
       double pq = 0.0;
-      for_nodes_nb<8>(
+      for_nodes_nb<NBC>(
           nx, ny, pt,
           [&](int, int, int k) {
-            const double kz = apply_k(z, k, pitch);
-            const double pk = it == 0 ? z[k] : fma(beta, p[k], z[k]);
+            const double kz = apply_k64(z, k, pitch);
+            const double zk = (double)z[k];
+            const double pk = it == 0 ? zk : fma(beta, p[k], zk);
             const double qk = it == 0 ? kz : fma(beta, q[k], kz);
             return double2{pk, qk};
           },
@@ -434,23 +477,24 @@ struct Solver {
       }
       const double alpha = rho / pq;
       double rn = 0.0;
-      for_nodes_nb<8>(
+      for_nodes_nb<NBC>(
           nx, ny, pt,
           [&](int, int, int k) { return double2{fma(alpha, p[k], x[k]), fma(-alpha, q[k], r[k])}; },
           [&](int k, double2 v) {
             x[k] = v.x;
             r[k] = v.y;
-            z0[k] = wd * v.y;  // the next V-cycle's first smoothing step from zero
+            z0[k] = VT(wd * v.y);  // the next V-cycle's first smoothing step from zero
             rn = fma(v.y, v.y, rn);
           });
       rr = allreduce1(rn, SLOT_RR);
       rho_old = rho;
+      alpha_old = alpha;
       ++it;
     }
     // True residual of the returned iterate.
     double rt = 0.0;
     for_nodes(nx, ny, pt, [&](int, int, int k) {
-      const double rk = f[k] - apply_k(x, k, pitch);
+      const double rk = f[k] - apply_k64(x, k, pitch);
       rt = fma(rk, rk, rt);
     });
     rt = allreduce1(rt, SLOT_TRUE);
@@ -469,15 +513,20 @@ struct Solver {
     const bool cl_on = C > 1;
     const double wd = d.wd;
     const double* v = d.f;
-    double* z0 = F.z[0];
-    for_nodes(F.nx, F.ny, part(cl_on), [&](int, int, int k) { z0[k] = wd * v[k]; });
+    VT* z0 = Z(d.L, 0);
+    for_nodes(F.nx, F.ny, part(cl_on), [&](int, int, int k) { z0[k] = VT(wd * v[k]); });
     sync(cl_on);
-    vcycle(v, nullptr);
-    const double* z = F.z[final_buf(d.L)];
-    copy_out(z);
+    double u = 0.0, w = 0.0;
+    vcycle(v, nullptr, nullptr, u, w);
+    const VT* z = Z(d.L, final_buf(d.L));
+    const int n = (F.nx + 1) * (F.ny + 1);
+    const int per = (n + C - 1) / C;
+    const int a = rank * per, e = min(n, a + per);
+    for (int k = a + threadIdx.x; k < e; k += PNT) d.x[k] = (double)z[k];  // zero on the boundary
+    sync(cl_on);
   }
 
-  // y = K v with v read as zero on the boundary.
+  // y = K v (float64) with v read as zero on the boundary.
   __device__ void apply() {
     const PLevel& F = d.lv[d.L];
     const int nx = F.nx, ny = F.ny, pitch = nx + 1;
@@ -492,36 +541,23 @@ struct Solver {
                        (vv(-1, 1) + vv(0, 1) + vv(1, 1));
       y[k] = (8.0 * v[k] - s) * (1.0 / 3.0);
     });
-    zero_boundary(y);
-    sync(C > 1);
-  }
-
-  // out = z at every node (z is zero on the boundary).
-  __device__ void copy_out(const double* z) {
-    const PLevel& F = d.lv[d.L];
-    const int n = (F.nx + 1) * (F.ny + 1);
-    const int per = (n + C - 1) / C;
-    const int a = rank * per, e = min(n, a + per);
-    for (int k = a + threadIdx.x; k < e; k += PNT) d.x[k] = z[k];
-    sync(C > 1);
-  }
-
-  __device__ void zero_boundary(double* y) {
-    if (rank != 0) return;
-    const PLevel& F = d.lv[d.L];
-    const int nx = F.nx, ny = F.ny, pitch = nx + 1;
-    for (int t = threadIdx.x; t < nx + 1; t += PNT) {
-      y[t] = 0.0;
-      y[ny * pitch + t] = 0.0;
+    if (rank == 0) {
+      for (int t = threadIdx.x; t < nx + 1; t += PNT) {
+        y[t] = 0.0;
+        y[ny * pitch + t] = 0.0;
+      }
+      for (int t = threadIdx.x; t < ny + 1; t += PNT) {
+        y[t * pitch] = 0.0;
+        y[t * pitch + nx] = 0.0;
+      }
     }
-    for (int t = threadIdx.x; t < ny + 1; t += PNT) {
-      y[t * pitch] = 0.0;
-      y[t * pitch + nx] = 0.0;
-    }
+    sync(C > 1);
   }
 };
 
-// One cluster of C CTAs per descriptor (right-hand side).
+// One cluster of C CTAs per descriptor (right-hand side); VT is the V-cycle's
+// value type.
+template <typename VT>
 __global__ void __launch_bounds__(PNT, 1) poisson_cluster_kernel(const PDesc* __restrict__ descs, int C) {
   __shared__ PDesc sd;
   __shared__ PShared sh;
@@ -534,7 +570,7 @@ __global__ void __launch_bounds__(PNT, 1) poisson_cluster_kernel(const PDesc* __
     for (int i = threadIdx.x; i < (int)(sizeof(PDesc) / sizeof(int)); i += PNT) t[i] = s[i];
   }
   __syncthreads();
-  Solver s{sd, sh, rank, C, cl};
+  Solver<VT> s{sd, sh, rank, C, cl};
   if (sd.mode == PMODE_SOLVE) s.solve();
   else if (sd.mode == PMODE_PRECOND) s.precondition();
   else s.apply();
@@ -594,6 +630,7 @@ __global__ void __launch_bounds__(PNT) poisson_coarsest_kernel(int nx0, int ny0,
 
 struct mto_poisson {
   int device = 0, nelx = 0, nely = 0, L = 0, fl = 0, C = 1, n0 = 0;
+  bool mixed = false;  // float32 V-cycle
   mto_poisson_opts o{};
   cudaStream_t user_stream = nullptr, stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_a = nullptr, ev_b = nullptr;
@@ -711,6 +748,7 @@ PDesc make_desc(const mto_poisson* c, int k, int mode, const double* in, double*
   d.nu1 = c->o.nu1;
   d.nu2 = c->o.nu2;
   d.max_it = c->o.max_it;
+  d.flexible = c->mixed ? 1 : 0;
   d.tol2 = c->o.tol * c->o.tol;
   d.wd = c->o.omega * 3.0 / 8.0;
   d.n0 = c->n0;
@@ -749,7 +787,10 @@ mto_status launch(mto_poisson* c, int n, int mode, const double* in, double* out
   cfg.attrs = at;
   cfg.numAttrs = 1;
   c->launches += 1;
-  PCK(cudaLaunchKernelEx(&cfg, poisson_cluster_kernel, (const PDesc*)c->d_desc, c->C));
+  if (c->mixed)
+    PCK(cudaLaunchKernelEx(&cfg, poisson_cluster_kernel<float>, (const PDesc*)c->d_desc, c->C));
+  else
+    PCK(cudaLaunchKernelEx(&cfg, poisson_cluster_kernel<double>, (const PDesc*)c->d_desc, c->C));
   return MTO_OK;
 }
 
@@ -767,9 +808,9 @@ mto_status leave(mto_poisson* c) {
 }
 
 // Largest cluster size (power of two, <= want) that the device can schedule
-// for this kernel.
-int usable_cluster(int want) {
-  cudaFuncSetAttribute(poisson_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+// for the kernel of V-cycle type VT.
+template <typename VT> int usable_cluster(int want) {
+  cudaFuncSetAttribute(poisson_cluster_kernel<VT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaGetLastError();
   for (int C = want; C > 1; C >>= 1) {
     cudaLaunchConfig_t cfg = {};
@@ -783,7 +824,7 @@ int usable_cluster(int want) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, poisson_cluster_kernel, &cfg) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveClusters(&clusters, poisson_cluster_kernel<VT>, &cfg) == cudaSuccess &&
         clusters > 0)
       return C;
     cudaGetLastError();
@@ -804,6 +845,7 @@ void mto_poisson_default_opts(mto_poisson_opts* o) {
   o->nu2 = 2;
   o->n_coarsen = 3;
   o->cluster_ctas = 0;
+  o->precision = MTO_PRECISION_FP64;
 }
 
 void mto_poisson_destroy(mto_poisson* c) {
@@ -844,7 +886,7 @@ static mto_status poisson_create_impl(mto_poisson* c, int device, void* stream) 
     while (want < PMAXC && (long long)want * LOCAL_MAX_NODES < interior) want <<= 1;
   }
   if (interior <= LOCAL_MAX_NODES) want = 1;
-  c->C = want > 1 ? usable_cluster(want) : 1;
+  c->C = want > 1 ? (c->mixed ? usable_cluster<float>(want) : usable_cluster<double>(want)) : 1;
   // Levels small enough for CTA 0 alone.
   c->fl = c->L;
   if (c->C > 1) {
@@ -894,7 +936,8 @@ mto_status mto_poisson_create(mto_poisson** out, int nelx, int nely, const mto_p
                      o.cluster_ctas == 4 || o.cluster_ctas == 8 || o.cluster_ctas == 16;
   if (nelx < 2 || nely < 2 || device < 0 || !(o.tol >= 0.0) || o.max_it < 0 || !(o.omega > 0.0) ||
       !(o.omega <= 1.0) || o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.n_coarsen < 1 ||
-      o.n_coarsen >= PMAXL || !cl_ok)
+      o.n_coarsen >= PMAXL || !cl_ok ||
+      (o.precision != MTO_PRECISION_FP64 && o.precision != MTO_PRECISION_MIXED))
     return MTO_ERR_ARG;
   if (nelx % (1 << o.n_coarsen) || nely % (1 << o.n_coarsen)) return MTO_ERR_UNSUPPORTED_MESH;
   const int nx0 = nelx >> o.n_coarsen, ny0 = nely >> o.n_coarsen;
@@ -907,6 +950,7 @@ mto_status mto_poisson_create(mto_poisson** out, int nelx, int nely, const mto_p
   c->nely = nely;
   c->o = o;
   c->L = o.n_coarsen;
+  c->mixed = o.precision == MTO_PRECISION_MIXED;
   const mto_status s = poisson_create_impl(c, device, cuda_stream);
   if (s != MTO_OK) {
     cudaGetLastError();

@@ -146,3 +146,34 @@ def test_iteration_limit_and_two_grid_case(mto):
     assert rel(u.cpu().numpy(), poisson.solve_direct(n, n, f)) <= 1e-8
     assert abs(st["iters"] - ref["iters"]) <= 1
     p.close()
+
+
+@pytest.mark.parametrize("n,C", [(64, 0), (256, 0), (128, 4), (200, 1)])
+def test_mixed_precision_vcycle_and_solve(mto, n, C):
+    # Float32 V-cycle inside the float64 CG (flexible beta): the V-cycle
+    # against the oracle's float64 one (2^-24 per operation, amplified by
+    # residual cancellation over the grids: bar 2e-5, as for elasticity), the
+    # solve against the direct solution at tol 1e-10, the iteration count
+    # within 2 of the oracle's float64 pCGMG.
+    ny = 136 if n == 200 else n
+    nc = 3 if n == 200 else n.bit_length() - 2
+    p = mto.Poisson(n, ny, n_coarsen=nc, tol=1e-10, precision="mixed", cluster_ctas=C)
+    lv = poisson.build_hierarchy(n, ny, nc)
+    free = lv[-1].free
+    r = rand_nodal(n, ny, seed=7 * n)
+    z = p.apply_preconditioner(to_dev(r)).cpu().numpy()
+    zref = np.zeros(r.size)
+    zref[free] = multigrid.vcycle_preconditioner(lv, 0.6, 2, 2)(r.ravel()[free])
+    assert rel(z, zref) <= 2e-5, rel(z, zref)
+    f = rand_nodal(n, ny, seed=n + 1)
+    u, st = p.solve(to_dev(f))
+    ref = poisson.solve_pcgmg(n, ny, f, nc, tol=1e-10)
+    assert st["status"] == "MTO_OK", st
+    assert rel(u.cpu().numpy(), poisson.solve_direct(n, ny, f)) <= 1e-8
+    assert abs(st["iters"] - ref["iters"]) <= 2, (st["iters"], ref["iters"])
+    assert st["rel_res_true"] <= 1.1e-10
+    # Batched right-hand sides equal single solves bit for bit.
+    F = np.stack([f, rand_nodal(n, ny, seed=n + 2)])
+    U, _ = p.solve(to_dev(F))
+    assert torch.equal(U[0], u)
+    p.close()
