@@ -177,3 +177,27 @@ def test_mixed_precision_vcycle_and_solve(mto, n, C):
     U, _ = p.solve(to_dev(F))
     assert torch.equal(U[0], u)
     p.close()
+
+
+@pytest.mark.parametrize("nu1,nu2,omega,C", [(1, 1, 0.6, 0), (3, 3, 0.6, 0), (2, 1, 0.8, 2), (1, 3, 0.5, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_smoothing_options(mto, nu1, nu2, omega, C, prec):
+    # Other smoothing counts and weights of Alg. 1 / Sec. 2.3 (unequal counts
+    # make the V-cycle unsymmetric, so only the V-cycle and the solution are
+    # compared, not the iteration count), on a non-square mesh with a forced
+    # cluster size (C = 1: every grid in one CTA).
+    nx, ny, nc = 128, 64, 5
+    p = mto.Poisson(nx, ny, n_coarsen=nc, tol=1e-10, nu1=nu1, nu2=nu2, omega=omega,
+                    cluster_ctas=C, precision=prec, max_it=300)
+    lv = poisson.build_hierarchy(nx, ny, nc)
+    free = lv[-1].free
+    r = rand_nodal(nx, ny, seed=nu1 * 10 + nu2)
+    z = p.apply_preconditioner(to_dev(r)).cpu().numpy()
+    zref = np.zeros(r.size)
+    zref[free] = multigrid.vcycle_preconditioner(lv, omega, nu1, nu2)(r.ravel()[free])
+    assert rel(z, zref) <= (1e-12 if prec == "fp64" else 2e-5), rel(z, zref)
+    f = rand_nodal(nx, ny, seed=3)
+    u, st = p.solve(to_dev(f))
+    assert st["status"] == "MTO_OK", st
+    assert rel(u.cpu().numpy(), poisson.solve_direct(nx, ny, f)) <= 1e-8
+    p.close()
