@@ -16,6 +16,12 @@
  *   design fractions are [n_phase][nely][nelx];
  *   element local nodes run counter-clockwise from the bottom-left.
  *
+ * Alignment: nodal vectors on the device (f, u, v, y, r, z of the elasticity
+ * calls) are read and written as (u_x, u_y) pairs and must be 16-byte aligned
+ * (every cudaMalloc'd address is; an offset into one must be a whole number
+ * of nodes); misaligned ones are rejected with MTO_ERR_ARG before any device
+ * work.  Other device arrays need the natural alignment of their type.
+ *
  * Errors: every call returns an mto_status; nothing is thrown across the ABI.
  * A CUDA failure inside a call returns MTO_ERR_CUDA and leaves the context
  * in a state where mto_destroy is still valid.

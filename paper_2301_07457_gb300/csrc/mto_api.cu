@@ -1220,7 +1220,8 @@ mto_status mto_set_design(mto_ctx* c, int n_phase, const double* x_dev, const do
 mto_status mto_solve(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev,
                      mto_solve_stats* stats) {
   NvtxRange nvtx_range("mto_solve");
-  if (!c || n_rhs < 1 || n_rhs > MAX_RHS || !f_dev || !u_dev) return MTO_ERR_ARG;
+  if (!c || n_rhs < 1 || n_rhs > MAX_RHS || !f_dev || !u_dev || !aligned16(f_dev) || !aligned16(u_dev))
+    return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   const mto_status s = solve_rhs(c, n_rhs, f_dev, u_dev);
@@ -1244,7 +1245,8 @@ mto_status mto_last_stats(mto_ctx* c, mto_solve_stats* stats) {
 mto_status mto_compliance_grad(mto_ctx* c, int n_rhs, const double* f_dev, const double* u_dev,
                                double* compliance_dev, double* dcdx_dev) {
   NvtxRange nvtx_range("mto_compliance_grad");
-  if (!c || n_rhs < 1 || !f_dev || !u_dev || !compliance_dev) return MTO_ERR_ARG;
+  if (!c || n_rhs < 1 || !f_dev || !u_dev || !compliance_dev || !aligned16(f_dev) || !aligned16(u_dev))
+    return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   ST(enqueue_compliance(c, n_rhs, f_dev, u_dev, compliance_dev, dcdx_dev));
@@ -1346,7 +1348,8 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
 
 mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, const double* v_dev,
                               double* y_dev) {
-  if (!c || !v_dev || !y_dev || level < 0 || level > c->L) return MTO_ERR_ARG;
+  if (!c || !v_dev || !y_dev || level < 0 || level > c->L || !aligned16(v_dev) || !aligned16(y_dev))
+    return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   LevelBuf& B = c->lv[level];
@@ -1394,7 +1397,7 @@ mto_status mto_apply_operator(mto_ctx* c, int level, int use_vcycle_operator, co
 }
 
 mto_status mto_apply_preconditioner(mto_ctx* c, const double* r_dev, double* z_dev) {
-  if (!c || !r_dev || !z_dev) return MTO_ERR_ARG;
+  if (!c || !r_dev || !z_dev || !aligned16(r_dev) || !aligned16(z_dev)) return MTO_ERR_ARG;
   if (!c->has_design) return MTO_ERR_STATE;
   ST(enter(c));
   LevelBuf& B = c->lv[c->L];

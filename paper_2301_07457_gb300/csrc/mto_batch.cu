@@ -122,7 +122,8 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
     if (!c || c->device != device || c->timing) return MTO_ERR_ARG;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return MTO_ERR_ARG;  // a context has one set of buffers
-    if (!it.x_dev || !it.E_phase || !it.f_dev || !it.u_dev || it.n_rhs < 1 || it.n_rhs > MAX_RHS ||
+    if (!it.x_dev || !it.E_phase || !it.f_dev || !it.u_dev || !aligned16(it.f_dev) ||
+        !aligned16(it.u_dev) || it.n_rhs < 1 || it.n_rhs > MAX_RHS ||
         it.n_phase < 1 || it.n_phase > 16 || !(it.penal >= 1.0 && it.penal <= 64.0) ||
         (it.dcdx_dev && !it.compliance_dev))
       return MTO_ERR_ARG;

@@ -3,6 +3,7 @@
 // mto_batch.cu: batched graphs and the launch-shape tuner).
 #pragma once
 
+#include <cstdint>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -168,6 +169,10 @@ extern thread_local cudaError_t g_last_cuda;
 // cudaErrorMemoryAllocation, without calling cudaMalloc.
 cudaError_t device_alloc(void** p, size_t bytes);
 void device_free(void* p);
+
+// Nodal vectors are read and written as (u_x, u_y) pairs of 16 bytes: the
+// entry points reject caller pointers that are not 16-byte aligned.
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // An NVTX range around a public call (no cost without a profiler attached).
 struct NvtxRange {

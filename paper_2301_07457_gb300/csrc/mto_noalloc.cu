@@ -79,7 +79,8 @@ extern "C" mto_status mto_compliance_grad_noalloc(int nelx, int nely, double nu,
                                                   const double* u_dev, double* compliance_dev,
                                                   double* dcdx_dev, int device, void* cuda_stream) {
   if (nelx < 1 || nely < 1 || !(nu > -1.0 && nu < 0.5) || n_phase < 1 || n_phase > 16 || !E_phase ||
-      !(penal >= 1.0 && penal <= 64.0) || !f_dev || !u_dev || !compliance_dev ||
+      !(penal >= 1.0 && penal <= 64.0) || !f_dev || !u_dev || !compliance_dev || !aligned16(f_dev) ||
+      !aligned16(u_dev) ||
       (dcdx_dev && !x_dev))
     return MTO_ERR_ARG;
   const long long nodes = ((long long)nelx + 1) * ((long long)nely + 1);
