@@ -84,6 +84,8 @@ def parse():
                     help="level study: most outer optimiser iterations per mesh and level")
     ap.add_argument("--study-seconds", type=float, default=150.0,
                     help="level study: wall-time budget of the optimiser loop per mesh and level")
+    ap.add_argument("--study-meshes", default=None,
+                    help="level study: comma-separated subset of the meshes, e.g. 128x128,128x256")
     return ap.parse_args()
 
 
@@ -683,7 +685,11 @@ def run_level_study(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     T = TABLE2
-    for nelx, nely in PAPER_MESHES:
+    meshes = PAPER_MESHES
+    if args.study_meshes:
+        keep = set(args.study_meshes.split(","))
+        meshes = [m for m in PAPER_MESHES if f"{m[0]}x{m[1]}" in keep]
+    for nelx, nely in meshes:
         f = torch.from_numpy(load_top_edge(nelx, nely)).to(dev)
         x = torch.from_numpy(dirichlet_design(nelx, nely, 4, SEED)).to(dev)
         for l in range(2, 7):

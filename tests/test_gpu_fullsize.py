@@ -19,6 +19,9 @@ about two minutes and 13 GB of host memory) at tolerance 1e-10.  Bars:
     GPU reports;
     the energy identity |f.u - u^T K u| <= ||u|| ||f - K u|| (Cauchy-Schwarz)
     with u^T K u from the oracle's element energies;
+  * the W-cycle (mixed, gamma = 2) and the rediscretised coarse operators
+    (float64): the same residual, energy and sensitivity checks, and u within
+    1e-8 of the oracle's solution;
   * sensitivities: 4,096 seeded (phase, element) picks recomputed one by one
     by the oracle from the returned u, relative error <= 1e-12 (same u, same
     formula: only the order of roundings differs).
@@ -66,14 +69,17 @@ def gpu_solutions(mto, problem):
     xt = torch.from_numpy(x).to(DEV)
     ft = torch.from_numpy(f).to(DEV)
     out = {}
-    for prec in ("fp64", "mixed"):
-        mesh = mto.Mesh(N, N, n_coarsen=NC, tol=TOL, max_it=1000, precision=prec,
-                        rr_every=25, flexible=prec == "mixed")
+    variants = {"fp64": dict(precision="fp64"), "mixed": dict(precision="mixed"),
+                "mixed_w": dict(precision="mixed", gamma=2),
+                "fp64_redisc": dict(precision="fp64", coarse_kind="rediscretize")}
+    for name, kw in variants.items():
+        mesh = mto.Mesh(N, N, n_coarsen=NC, tol=TOL, max_it=1000, rr_every=25,
+                        flexible=kw["precision"] == "mixed", **kw)
         mesh.set_design(xt, EP, 3.0)
         mesh.autotune()
         u, st = mesh.solve(ft)
         C, g = mesh.compliance_grad(ft, u)
-        out[prec] = {"u": u.cpu().numpy(), "st": st, "C": C.item(), "g": g.cpu().numpy()}
+        out[name] = {"u": u.cpu().numpy(), "st": st, "C": C.item(), "g": g.cpu().numpy()}
         mesh.close()
         del u, g
     torch.cuda.empty_cache()
@@ -84,7 +90,7 @@ def rel(a, b):
     return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_w", "fp64_redisc"])
 def test_fullsize_residual_energy_and_sensitivities(problem, gpu_solutions, prec):
     x, f, E = problem
     sol = gpu_solutions[prec]
@@ -139,3 +145,14 @@ def test_fullsize_mixed_matches_oracle_and_fp64(gpu_solutions, oracle_solution):
     print(f"mixed 2048^2: iters {mixed['st']['iters']}, u rel vs oracle {e_or:.3e}, vs fp64 {e_64:.3e}")
     assert e_or <= 1e-8
     assert e_64 <= 1e-8
+
+
+@pytest.mark.parametrize("variant", ["mixed_w", "fp64_redisc"])
+def test_fullsize_other_cycles_match_oracle(gpu_solutions, oracle_solution, variant):
+    # The W-cycle (gamma = 2 below the finest grid, Alg. 1) and the
+    # rediscretised coarse operators (Sec. 2.1) change the preconditioner,
+    # not the solution: u within the same 1e-8 of the oracle's V-cycle solve.
+    sol = gpu_solutions[variant]
+    err = rel(sol["u"], oracle_solution["u"])
+    print(f"{variant} 2048^2: iters {sol['st']['iters']}, u rel vs oracle {err:.3e}")
+    assert err <= 1e-8
