@@ -297,6 +297,56 @@ template <typename VT> struct Solver {
         });
   }
 
+  // Float32 V-cycle only: the residual formed on the fly at the nine fine
+  // nodes of each coarse node inside the restriction, and the prolongation
+  // formed on the fly at the node and its neighbours inside the first
+  // post-smoothing sweep.  The recomputation costs float32 operations, which
+  // are cheap here, and saves two barriers per grid.
+  template <typename BT>
+  __device__ void restrict_fused(int l, const VT* zpre, const BT* b, bool cluster) {
+    const int pf = d.lv[l].nx + 1;
+    const PLevel& c = d.lv[l - 1];
+    VT* bc = B(l - 1);
+    VT* z0 = Z(l - 1, 0);
+    const VT wd = VT(d.wd), h = VT(0.5), qt = VT(0.25), third = VT(1.0 / 3.0);
+    const bool first = l - 1 >= 1;
+    for_nodes_nb<2>(
+        c.nx, c.ny, part(cluster),
+        [&](int I, int J, int) {
+          const int k = 2 * J * pf + 2 * I;
+          auto res = [&](int kk) { return VT(b[kk]) - (VT(8) * zpre[kk] - nbsum_t(zpre, kk, pf)) * third; };
+          return res(k) + h * ((res(k - 1) + res(k + 1)) + (res(k - pf) + res(k + pf))) +
+                 qt * ((res(k - pf - 1) + res(k - pf + 1)) + (res(k + pf - 1) + res(k + pf + 1)));
+        },
+        [&](int kc, VT v) {
+          bc[kc] = v;
+          if (first) z0[kc] = wd * v;
+        });
+  }
+
+  template <typename BT>
+  __device__ void prolong_sweep(int l, const VT* zpre, const VT* zc, VT* dst, const BT* b, bool cluster,
+                                const double* dotv, const double* dotq, double& acc, double& accq) {
+    const PLevel& lv = d.lv[l];
+    const int pitch = lv.nx + 1, pc = d.lv[l - 1].nx + 1;
+    const VT wd = VT(d.wd), cz = VT(1.0 - 8.0 * d.wd / 3.0), cs = VT(d.wd / 3.0);
+    for_nodes_nb<2>(
+        lv.nx, lv.ny, part(cluster),
+        [&](int i, int j, int k) {
+          auto zf = [&](int di, int dj) {
+            return zpre[k + dj * pitch + di] + prolong_t(zc, pc, i + di, j + dj);
+          };
+          const VT s = (zf(-1, -1) + zf(0, -1) + zf(1, -1)) + (zf(-1, 0) + zf(1, 0)) +
+                       (zf(-1, 1) + zf(0, 1) + zf(1, 1));
+          return fma(cz, zf(0, 0), fma(wd, VT(b[k]), cs * s));
+        },
+        [&](int k, VT v) {
+          dst[k] = v;
+          if (dotv) acc = fma((double)v, dotv[k], acc);
+          if (dotq) accq = fma((double)v, dotq[k], accq);
+        });
+  }
+
   // Coarsest grid: z = K_0^-1 b (float64 dense inverse, one warp per row).
   __device__ void coarsest() {
     const PLevel& c = d.lv[0];
@@ -324,9 +374,13 @@ template <typename VT> struct Solver {
       cur ^= 1;
       sync(cluster);
     }
-    residual(l, Z(l, cur), b, Z(l, cur ^ 1), cluster);
-    sync(cluster);
-    restrict_to(l, Z(l, cur ^ 1), cluster);
+    if constexpr (sizeof(VT) == 4) {
+      restrict_fused(l, Z(l, cur), b, cluster);
+    } else {
+      residual(l, Z(l, cur), b, Z(l, cur ^ 1), cluster);
+      sync(cluster);
+      restrict_to(l, Z(l, cur ^ 1), cluster);
+    }
     sync(cluster);
   }
 
@@ -337,8 +391,17 @@ template <typename VT> struct Solver {
   __device__ void ascend(int l, const BT* b, bool cluster, const double* dotv, const double* dotq,
                          double& acc, double& accq) {
     int cur = pre_buf();
-    prolong_add(l, Z(l, cur), Z(l - 1, final_buf(l - 1)), cluster);
-    for (int s = 0; s < d.nu2; ++s) {
+    int s0 = 0;
+    if constexpr (sizeof(VT) == 4) {
+      const bool last = d.nu2 == 1;
+      prolong_sweep(l, Z(l, cur), Z(l - 1, final_buf(l - 1)), Z(l, cur ^ 1), b, cluster,
+                    last ? dotv : nullptr, last ? dotq : nullptr, acc, accq);
+      cur ^= 1;
+      s0 = 1;
+    } else {
+      prolong_add(l, Z(l, cur), Z(l - 1, final_buf(l - 1)), cluster);
+    }
+    for (int s = s0; s < d.nu2; ++s) {
       sync(cluster);
       const bool last = s == d.nu2 - 1;
       sweep(l, Z(l, cur), Z(l, cur ^ 1), b, cluster, last ? dotv : nullptr, last ? dotq : nullptr, acc,
