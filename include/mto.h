@@ -28,9 +28,10 @@
  *
  * Streams: the context runs its device work on a private stream that is
  * ordered after the caller's stream (given at creation) on entry to every
- * call, and before it on return.  mto_set_design, mto_solve, mto_run_host
- * and mto_last_stats synchronise (the solve polls its convergence flag);
- * mto_compliance_grad and the diagnostics only enqueue.
+ * call, and before it on return.  mto_set_design, mto_solve, mto_run_host,
+ * mto_run_host_wait and mto_last_stats synchronise (the solve polls its
+ * convergence flag); mto_compliance_grad, mto_run_host_async and the
+ * diagnostics only enqueue.
  *
  * Threads: a context is not thread-safe; use one context per host thread.
  *
@@ -214,6 +215,30 @@ mto_status mto_run_host(mto_ctx* ctx, int n_phase, const double* x_host, const d
                         double penal, int n_rhs, const double* f_host, double* u_host,
                         double* compliance_host, double* dcdx_host, mto_solve_stats* stats);
 
+/* The same call, pipelined: mto_run_host_async enqueues it and returns at
+ * once; mto_run_host_wait blocks until the oldest outstanding call has
+ * finished and its outputs are in the host arrays, and returns that call's
+ * status and statistics (stats may be NULL).  Arguments, layouts and results
+ * are those of mto_run_host, bit for bit.  At most two calls are outstanding:
+ * while call k computes, call k+1's x and f travel to the device and call
+ * k-1's u and sensitivities travel back, on their own streams.  For that
+ * overlap the host arrays must be pinned (pageable ones work, but their
+ * copies serialise with the host thread).  Every host array of a call belongs
+ * to the library until the wait that returns that call: the caller neither
+ * writes the inputs nor reads the outputs before then.  Errors: MTO_ERR_ARG
+ * as mto_run_host; MTO_ERR_STATE for a third outstanding call, for an async
+ * call while kernel timing is on, for a wait with nothing outstanding, and
+ * for mto_run_host while pipelined calls are outstanding; MTO_ERR_BREAKDOWN
+ * from the wait when the design's coarsest factorisation broke down.  Other
+ * entry points may be called in between: their device work is ordered after
+ * the outstanding calls' kernels.  mto_destroy waits for outstanding calls.
+ * The paper has no counterpart: it serves optimisation loops that keep the
+ * design on the host. */
+mto_status mto_run_host_async(mto_ctx* ctx, int n_phase, const double* x_host, const double* E_phase,
+                              double penal, int n_rhs, const double* f_host, double* u_host,
+                              double* compliance_host, double* dcdx_host);
+mto_status mto_run_host_wait(mto_ctx* ctx, mto_solve_stats* stats);
+
 /* Diagnostics for per-kernel checks.
  * level: 0 = coarsest ... n_coarsen = finest (the numbering of Alg. 1).
  * Vectors are device float64 in the level's own layout [ny_l+1][nx_l+1][2]
@@ -237,9 +262,8 @@ mto_status mto_get_moduli(mto_ctx* ctx, double* E_dev);
 
 /* Compliance and sensitivities with no device allocation and no context.
  * The paper has no counterpart: this exists for callers that cannot allocate
- * device memory -- code running while its stream is being captured into a
- * CUDA graph (cudaMalloc is not allowed during capture), hosts whose memory
- * pool owns the device's memory and forbids other allocations, and
+ * device memory -- hosts whose memory pool owns the device's memory and
+ * forbids other allocations, and
  * latency-critical loops that cannot take the device-wide synchronisation of
  * cudaMalloc/cudaFree.  Computes, for one load case on an nelx x nely mesh,
  * compliance_dev[0] = f . u and (if dcdx_dev != NULL) dcdx_dev[i][e] =
@@ -252,8 +276,8 @@ mto_status mto_get_moduli(mto_ctx* ctx, double* E_dev);
  * Scratch: a fixed 512 KiB device array inside the library, held on every GPU
  * that loads it until the process exits; meshes above 33,554,432 nodes are
  * rejected with MTO_ERR_UNSUPPORTED_MESH.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call shares the
+ * the array's device address (cudaGetSymbolAddress) with that device current.
+ * Every call shares the
  * array and clears its counter at the start; calls whose work overlaps on the
  * GPU (other streams, other host threads) race and must be serialised by the
  * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */

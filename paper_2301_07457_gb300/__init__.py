@@ -106,12 +106,14 @@ class Mesh:
         # on the device are still those of a given design.
         self.design_version = 0
         self.last_solve_stats = None
+        self._pending = []  # host arrays of outstanding run_host_async calls
 
     # -- lifecycle -----------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
-            self._lib.mto_destroy(self._h)
+            self._lib.mto_destroy(self._h)  # waits for outstanding host calls
             self._h = ctypes.c_void_p()
+            self._pending = []
 
     def __del__(self):
         try:
@@ -194,7 +196,54 @@ class Mesh:
                 C.ctypes.data_as(ctypes.c_void_p),
                 g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, ctypes.byref(st))
         _lib.check(code, "mto_run_host")
+        self._host_design(x.shape[0], E_phase, penal)
         return u, C, g, st.as_dict()
+
+    def _host_design(self, n_phase, E_phase, penal):
+        # A host call leaves its design on the device, as set_design does.
+        self.n_phase, self.E_phase, self.penal = n_phase, list(E_phase), float(penal)
+        self.design_version += 1
+
+    def run_host_async(self, x, E_phase, penal, f, want_grad=True):
+        """Enqueue run_host without waiting (at most two calls outstanding).
+
+        x and f: float64 host arrays; pinned CPU tensors are used in place
+        (the caller leaves them unchanged until the matching run_host_wait),
+        anything else is first copied into pinned memory.  The outputs are
+        pinned and handed back by run_host_wait, oldest call first.
+        """
+        def pinned(a):
+            if isinstance(a, torch.Tensor) and a.device.type == "cpu" and a.dtype == torch.float64 \
+                    and a.is_contiguous() and a.is_pinned():
+                return a
+            t = torch.as_tensor(a, dtype=torch.float64).contiguous()
+            return t.pin_memory()
+        xt, ft = pinned(x), pinned(f)
+        n_rhs = ft.shape[0] if ft.dim() == 4 else 1
+        u = torch.empty(ft.shape, dtype=torch.float64, pin_memory=True)
+        C = torch.empty(n_rhs, dtype=torch.float64, pin_memory=True)
+        g = torch.empty(xt.shape, dtype=torch.float64, pin_memory=True) if want_grad else None
+        E = (ctypes.c_double * len(E_phase))(*[float(e) for e in E_phase])
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_run_host_async(
+                self._h, xt.shape[0], ctypes.c_void_p(xt.data_ptr()), E, float(penal), n_rhs,
+                ctypes.c_void_p(ft.data_ptr()), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                ctypes.c_void_p(g.data_ptr()) if g is not None else None)
+        _lib.check(code, "mto_run_host_async")
+        self._pending.append((xt, ft, u, C, g))
+        self._host_design(xt.shape[0], E_phase, penal)
+
+    def run_host_wait(self):
+        """Result of the oldest outstanding run_host_async: (u, C, g, stats),
+        numpy views of pinned buffers (g None without gradients)."""
+        st = SolveStats()
+        with torch.cuda.device(self.device):
+            code = self._lib.mto_run_host_wait(self._h, ctypes.byref(st))
+        if code == _lib.ERR_STATE and not self._pending:
+            _lib.check(code, "mto_run_host_wait")
+        _, _, u, C, g = self._pending.pop(0)
+        _lib.check(code, "mto_run_host_wait")
+        return u.numpy(), C.numpy(), g.numpy() if g is not None else None, st.as_dict()
 
     # -- diagnostics ---------------------------------------------------------
     def level_shape(self, level):

@@ -109,6 +109,9 @@ SIGNATURES = {
     "mto_compliance_grad": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "mto_run_host": (ctypes.c_int, [_P, ctypes.c_int, _P, _D, ctypes.c_double, ctypes.c_int, _P, _P,
                                     _P, _P, ctypes.POINTER(SolveStats)]),
+    "mto_run_host_async": (ctypes.c_int, [_P, ctypes.c_int, _P, _D, ctypes.c_double, ctypes.c_int, _P, _P,
+                                          _P, _P]),
+    "mto_run_host_wait": (ctypes.c_int, [_P, ctypes.POINTER(SolveStats)]),
     "mto_apply_operator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "mto_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
     "mto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),

@@ -69,7 +69,10 @@ mto_status dalloc(mto_ctx* c, void** out, size_t bytes) {
     return MTO_ERR_OOM;
   }
   c->allocs.push_back(*out);
-  if (cudaMemset(*out, 0, bytes) != cudaSuccess) return MTO_ERR_CUDA;
+  // The zero fill runs on the legacy stream, which the context's non-blocking
+  // streams do not order against: wait for it here.
+  if (cudaMemset(*out, 0, bytes) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
+    return MTO_ERR_CUDA;
   return MTO_OK;
 }
 
@@ -873,8 +876,12 @@ mto_status ensure_slots(mto_ctx* c, int want, int* got) {
 
 namespace {
 
-// Solves right-hand sides [0, n_rhs) and fills c->last; one host sync.
-mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) {
+// Enqueues right-hand sides [0, n_rhs) (no host synchronisation): the events
+// ev0 / ev1 bracket the device work on the context's stream and the
+// right-hand sides' statistics are copied to stats_host (pinned) behind it.
+// *S_out is the number of workspaces used (solve_rhs_finish needs it).
+mto_status solve_rhs_enqueue(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev,
+                             RhsStats* stats_host, cudaEvent_t ev0, cudaEvent_t ev1, int* S_out) {
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
   c->cs = c->stream;
   const bool polled = c->timing || c->no_while;
@@ -900,8 +907,9 @@ mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) 
       }
     }
   }
+  *S_out = S;
   auto slot_of = [&](int k) { return k % S == 0 ? c : c->slots[k % S - 1]; };
-  CK(cudaEventRecord(c->ev_a, c->stream));
+  CK(cudaEventRecord(ev0, c->stream));
   if (S > 1) {
     CK(cudaEventRecord(c->ev_slot, c->stream));
     for (int k = 1; k < S; ++k) CK(cudaStreamWaitEvent(c->slots[k - 1]->stream, c->ev_slot, 0));
@@ -924,16 +932,21 @@ mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) 
     CK(cudaStreamWaitEvent(c->stream, w->ev_slot, 0));
   }
   c->cs = c->stream;
-  CK(cudaEventRecord(c->ev_b, c->stream));
-  CK(cudaMemcpyAsync(c->rhs_stats_host, c->rhs_stats, sizeof(RhsStats) * n_rhs,
-                     cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+  CK(cudaEventRecord(ev1, c->stream));
+  CK(cudaMemcpyAsync(stats_host, c->rhs_stats, sizeof(RhsStats) * n_rhs, cudaMemcpyDeviceToHost,
+                     c->stream));
+  return MTO_OK;
+}
+
+// Statistics of completed right-hand sides (stats_host filled, ms the device
+// time of the solve): fills c->last and returns the worst status.
+mto_status solve_rhs_finish(mto_ctx* c, int n_rhs, const RhsStats* stats_host, float ms, int S,
+                            float ms_setup) {
+  auto slot_of = [&](int k) { return k % S == 0 ? c : c->slots[k % S - 1]; };
   mto_status worst = MTO_OK;
   int total = 0;
   for (int k = 0; k < n_rhs; ++k) {
-    const RhsStats& r = c->rhs_stats_host[k];
+    const RhsStats& r = stats_host[k];
     total += r.iter;
     if (!(c->timing || c->no_while)) {
       // The loop body (two iterations) ran max(1, ceil(iter / 2)) times.
@@ -947,15 +960,25 @@ mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) 
     c->launches += w->launches;
     w->launches = 0;
   }
-  const RhsStats& r = c->rhs_stats_host[n_rhs - 1];
+  const RhsStats& r = stats_host[n_rhs - 1];
   const double fn = std::sqrt(r.ff);
   c->last.iters = total;
   c->last.converged = worst == MTO_OK;
   c->last.rel_res_rec = fn > 0 ? std::sqrt(r.rr) / fn : 0.0;
   c->last.rel_res_true = fn > 0 ? std::sqrt(r.rr_true) / fn : 0.0;
   c->last.ms_solve = ms;
-  c->last.ms_setup = c->ms_setup;
+  c->last.ms_setup = ms_setup;
   return worst;
+}
+
+// Solves right-hand sides [0, n_rhs) and fills c->last; one host sync.
+mto_status solve_rhs(mto_ctx* c, int n_rhs, const double* f_dev, double* u_dev) {
+  int S = 1;
+  ST(solve_rhs_enqueue(c, n_rhs, f_dev, u_dev, c->rhs_stats_host, c->ev_a, c->ev_b, &S));
+  CK(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+  return solve_rhs_finish(c, n_rhs, c->rhs_stats_host, ms, S, c->ms_setup);
 }
 
 }  // namespace
@@ -1014,9 +1037,19 @@ void mto_destroy(mto_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->down) cudaStreamSynchronize(c->down);
   for (mto_ctx* s : c->slots) mto_destroy(s);
   c->slots.clear();
   if (c->ev_slot) cudaEventDestroy(c->ev_slot);
+  for (HostCall& h : c->hq) {
+    if (h.stats) cudaFreeHost(h.stats);
+    if (h.err) cudaFreeHost(h.err);
+    for (cudaEvent_t e : {h.setup0, h.setup1, h.t0, h.t1, h.in, h.done})
+      if (e) cudaEventDestroy(e);
+  }
+  for (cudaEvent_t e : {c->ev_stage_free[0], c->ev_stage_free[1], c->ev_u_out, c->ev_g_out, c->ev_cmp})
+    if (e) cudaEventDestroy(e);
+  if (c->down) cudaStreamDestroy(c->down);
   invalidate_graphs(c);
   for (void* p : c->allocs) device_free(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
@@ -1260,12 +1293,12 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
   if (!c || !x_host || n_rhs < 1 || n_rhs > MAX_RHS || !f_host || !u_host || !compliance_host ||
       !valid_design(n_phase, E_phase, penal))
     return MTO_ERR_ARG;
+  if (c->hq_count > 0) return MTO_ERR_STATE;  // pipelined calls still in flight
   const size_t nel = (size_t)c->nelx * c->nely;
   const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
   ST(grow(c, &c->xdes, &c->xdes_cap, (size_t)n_phase * nel));
-  size_t fcap = c->hf_cap;
   ST(grow(c, &c->hf, &c->hf_cap, (size_t)n_rhs * nd));
-  ST(grow(c, &c->hu, &fcap, (size_t)n_rhs * nd));
+  ST(grow(c, &c->hu, &c->hu_cap, (size_t)n_rhs * nd));
   size_t ccap = (size_t)c->hc_cap;
   ST(grow(c, &c->hc, &ccap, (size_t)n_rhs));
   c->hc_cap = (int)ccap;
@@ -1342,6 +1375,136 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
   CK(cudaStreamSynchronize(c->aux));
   CK(cudaStreamSynchronize(c->stream));
   ST(leave(c));
+  if (stats) *stats = c->last;
+  return s;
+}
+
+static mto_status hq_setup(mto_ctx* c) {
+  if (c->hq_ready) return MTO_OK;
+  CK(cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking));
+  for (HostCall& h : c->hq) {
+    CK(cudaMallocHost(&h.stats, sizeof(RhsStats) * MAX_RHS));
+    CK(cudaMallocHost(&h.err, sizeof(int)));
+    for (cudaEvent_t* e : {&h.setup0, &h.setup1, &h.t0, &h.t1}) CK(cudaEventCreate(e));
+    CK(cudaEventCreateWithFlags(&h.in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
+  }
+  for (cudaEvent_t* e : {&c->ev_stage_free[0], &c->ev_stage_free[1], &c->ev_u_out, &c->ev_g_out, &c->ev_cmp})
+    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  c->hq_ready = true;
+  return MTO_OK;
+}
+
+mto_status mto_run_host_async(mto_ctx* c, int n_phase, const double* x_host, const double* E_phase,
+                              double penal, int n_rhs, const double* f_host, double* u_host,
+                              double* compliance_host, double* dcdx_host) {
+  NvtxRange nvtx_range("mto_run_host_async");
+  if (!c || !x_host || n_rhs < 1 || n_rhs > MAX_RHS || !f_host || !u_host || !compliance_host ||
+      !valid_design(n_phase, E_phase, penal))
+    return MTO_ERR_ARG;
+  if (c->timing || c->hq_count >= 2) return MTO_ERR_STATE;
+  const size_t nel = (size_t)c->nelx * c->nely;
+  const size_t nd = 2 * (size_t)(c->nelx + 1) * (c->nely + 1);
+  ST(enter(c));
+  ST(hq_setup(c));
+  const int slot = (c->hq_head + c->hq_count) & 1;
+  HostCall& h = c->hq[slot];
+  // Buffers (grown ones keep their old allocation alive for a call in flight).
+  ST(grow(c, &c->xdes, &c->xdes_cap, (size_t)n_phase * nel));
+  ST(grow(c, &c->xstage[slot], &c->xstage_cap[slot], (size_t)n_phase * nel));
+  ST(grow(c, &c->fstage[slot], &c->fstage_cap[slot], (size_t)n_rhs * nd));
+  ST(grow(c, &c->hu, &c->hu_cap, (size_t)n_rhs * nd));
+  size_t ccap = (size_t)c->hc_cap;
+  ST(grow(c, &c->hc, &ccap, (size_t)n_rhs));
+  c->hc_cap = (int)ccap;
+  if (dcdx_host) ST(grow(c, &c->hg, &c->hg_cap, (size_t)n_phase * nel));
+  double* xs = c->xstage[slot];
+  double* fs = c->fstage[slot];
+  double *hu = c->hu, *hc = c->hc, *hg = c->hg;
+  c->cs = c->stream;
+  // Upload (side stream): once the call that last used this staging slot has
+  // consumed its inputs.
+  CK(cudaStreamWaitEvent(c->aux, c->ev_stage_free[slot], 0));
+  CK(cudaMemcpyAsync(xs, x_host, sizeof(double) * n_phase * nel, cudaMemcpyHostToDevice, c->aux));
+  CK(cudaMemcpyAsync(fs, f_host, sizeof(double) * n_rhs * nd, cudaMemcpyHostToDevice, c->aux));
+  CK(cudaEventRecord(h.in, c->aux));
+  // Design (compute stream, after the previous call's compute).
+  CK(cudaStreamWaitEvent(c->stream, h.in, 0));
+  CK(cudaEventRecord(h.setup0, c->stream));
+  CK(cudaMemcpyAsync(c->xdes, xs, sizeof(double) * n_phase * nel, cudaMemcpyDeviceToDevice, c->stream));
+  design_params(c, n_phase, E_phase, penal);
+  ST(enqueue_modulus(c, 0, c->nely));
+  ST(enqueue_hierarchy(c));
+  CK(cudaMemcpyAsync(h.err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaEventRecord(h.setup1, c->stream));
+  c->has_design = true;
+  // Solve from zero into hu, once the previous call's u has left.
+  CK(cudaStreamWaitEvent(c->stream, c->ev_u_out, 0));
+  CK(cudaMemsetAsync(hu, 0, sizeof(double) * n_rhs * nd, c->stream));
+  int S = 1;
+  ST(solve_rhs_enqueue(c, n_rhs, fs, hu, h.stats, h.t0, h.t1, &S));
+  c->cs = c->stream;
+  // Compliance and sensitivities, once the previous call's results have left.
+  CK(cudaStreamWaitEvent(c->stream, c->ev_g_out, 0));
+  ST(enqueue_compliance(c, n_rhs, fs, hu, hc, nullptr));
+  CK(cudaEventRecord(c->ev_cmp, c->stream));
+  const int nch = std::min(HOST_CHUNKS, c->nely);
+  auto rows = [&](int k) { return (int)((long long)c->nely * k / nch); };
+  if (dcdx_host) {
+    const long long nn = (long long)(c->nelx + 1) * (c->nely + 1);
+    for (int k = 0; k < nch; ++k) {
+      for (int r = 0; r < n_rhs; ++r)
+        KL(launch_sensitivity(c->nelx, c->nely, c->n_phase, c->xdes, c->ph, c->penal, c->ipenal,
+                              c->kf64, hu + 2 * nn * r, hg, r > 0, c->stream, c->num_sms, rows(k),
+                              rows(k + 1)));
+      CK(cudaEventRecord(c->ev_chunk[k], c->stream));
+    }
+  }
+  CK(cudaEventRecord(c->ev_stage_free[slot], c->stream));
+  // Download (own stream).
+  CK(cudaStreamWaitEvent(c->down, c->ev_cmp, 0));
+  CK(cudaMemcpyAsync(u_host, hu, sizeof(double) * n_rhs * nd, cudaMemcpyDeviceToHost, c->down));
+  CK(cudaEventRecord(c->ev_u_out, c->down));
+  CK(cudaMemcpyAsync(compliance_host, hc, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, c->down));
+  if (dcdx_host) {
+    for (int k = 0; k < nch; ++k) {
+      CK(cudaStreamWaitEvent(c->down, c->ev_chunk[k], 0));
+      const int j0 = rows(k), j1 = rows(k + 1);
+      for (int p = 0; p < n_phase; ++p) {
+        const size_t off = (size_t)p * nel + (size_t)j0 * c->nelx;
+        CK(cudaMemcpyAsync(dcdx_host + off, hg + off, sizeof(double) * (size_t)(j1 - j0) * c->nelx,
+                           cudaMemcpyDeviceToHost, c->down));
+      }
+    }
+  }
+  CK(cudaEventRecord(c->ev_g_out, c->down));
+  CK(cudaEventRecord(h.done, c->down));
+  h.n_rhs = n_rhs;
+  h.S = S;
+  h.u_host = u_host;
+  h.c_host = compliance_host;
+  h.g_host = dcdx_host;
+  c->hq_count += 1;
+  return leave(c);
+}
+
+mto_status mto_run_host_wait(mto_ctx* c, mto_solve_stats* stats) {
+  NvtxRange nvtx_range("mto_run_host_wait");
+  if (!c) return MTO_ERR_ARG;
+  if (c->hq_count == 0) return MTO_ERR_STATE;
+  CK(cudaSetDevice(c->device));
+  HostCall& h = c->hq[c->hq_head];
+  CK(cudaEventSynchronize(h.done));
+  c->hq_head ^= 1;
+  c->hq_count -= 1;
+  float ms = 0.f, ms_setup = 0.f;
+  CK(cudaEventElapsedTime(&ms, h.t0, h.t1));
+  CK(cudaEventElapsedTime(&ms_setup, h.setup0, h.setup1));
+  if (*h.err) {
+    if (c->hq_count == 0) c->has_design = false;  // unless a later call replaced the design
+    return MTO_ERR_BREAKDOWN;
+  }
+  const mto_status s = solve_rhs_finish(c, h.n_rhs, h.stats, ms, h.S, ms_setup);
   if (stats) *stats = c->last;
   return s;
 }

@@ -36,6 +36,18 @@ constexpr int MAX_TARGET_WARPS_PER_SM = 128;
 // transfer overlapping the kernels of its neighbours.
 constexpr int HOST_CHUNKS = 4;
 
+// One pipelined host call (mto_run_host_async) in flight: where its results
+// go, its statistics and the events that mark its progress.
+struct HostCall {
+  int n_rhs = 0, S = 1;
+  double *u_host = nullptr, *c_host = nullptr, *g_host = nullptr;
+  RhsStats* stats = nullptr;  // pinned [MAX_RHS]
+  int* err = nullptr;         // pinned: the design's factorisation failed
+  cudaEvent_t setup0 = nullptr, setup1 = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaEvent_t in = nullptr;    // inputs staged on the device
+  cudaEvent_t done = nullptr;  // results in host memory
+};
+
 }  // namespace mto
 
 struct mto_ctx {
@@ -96,7 +108,7 @@ struct mto_ctx {
   size_t xdes_cap = 0;
   // host-call staging (mto_run_host)
   double *hf = nullptr, *hu = nullptr, *hc = nullptr, *hg = nullptr;
-  size_t hf_cap = 0, hg_cap = 0;
+  size_t hf_cap = 0, hu_cap = 0, hg_cap = 0;
   int hc_cap = 0;
   // graph of two PCG iterations (host-polled loop, used when kernel timing is on)
   cudaGraphExec_t gexec = nullptr;
@@ -134,6 +146,19 @@ struct mto_ctx {
   std::vector<mto_ctx*> slots;
   mto_ctx* parent = nullptr;
   cudaEvent_t ev_slot = nullptr;
+  // Pipelined host calls: at most two in flight, in queue order from
+  // hq_head.  Inputs are staged in two device buffers (the call's slot), so
+  // that a call's upload overlaps the previous call's solve; results leave
+  // on their own stream, overlapping the next call.
+  mto::HostCall hq[2];
+  int hq_head = 0, hq_count = 0;
+  bool hq_ready = false;  // events, pinned buffers and the download stream exist
+  cudaStream_t down = nullptr;
+  double* xstage[2] = {nullptr, nullptr};
+  double* fstage[2] = {nullptr, nullptr};
+  size_t xstage_cap[2] = {0, 0}, fstage_cap[2] = {0, 0};
+  cudaEvent_t ev_stage_free[2] = {nullptr, nullptr};  // the slot's staged inputs are consumed
+  cudaEvent_t ev_u_out = nullptr, ev_g_out = nullptr, ev_cmp = nullptr;
 };
 
 namespace mto {

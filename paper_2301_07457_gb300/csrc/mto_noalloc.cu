@@ -1,9 +1,7 @@
 // Compliance and sensitivities without any device allocation.
 //
-// For callers that cannot allocate device memory: code that runs while one
-// of its streams is being captured into a CUDA graph (cudaMalloc is not
-// allowed there), hosts whose memory pool owns all of HBM and forbids other
-// allocations, and latency-critical loops that cannot afford the device-wide
+// For callers that cannot allocate device memory: hosts whose memory pool
+// owns all of HBM and forbids other allocations, and latency-critical loops that cannot afford the device-wide
 // synchronisation of cudaMalloc/cudaFree.  The context-based
 // mto_compliance_grad needs a context (allocated by mto_create_mesh); this
 // entry point needs none.  Its reduction scratch (one partial per block plus

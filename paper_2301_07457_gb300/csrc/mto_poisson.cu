@@ -762,8 +762,11 @@ mto_status grow_ws(mto_poisson* c, int n_rhs) {
     cudaGetLastError();
     return MTO_ERR_OOM;
   }
-  // Boundary entries are never written by the kernel: zero them once.
-  if (cudaMemset(ws, 0, sizeof(double) * w.total * n_rhs) != cudaSuccess) {
+  // Boundary entries are never written by the kernel: zero them once (on
+  // the legacy stream, which the solver's non-blocking stream does not order
+  // against, so wait for it).
+  if (cudaMemset(ws, 0, sizeof(double) * w.total * n_rhs) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess) {
     mto::device_free(ws);
     return fail_cuda(cudaGetLastError());
   }

@@ -1,8 +1,7 @@
 """The allocation-free compliance entry point against the context-based one.
 
 mto_compliance_grad_noalloc serves callers that cannot allocate device memory
-(for example while their stream is being captured into a CUDA graph, or when
-their memory pool owns the whole device).  It must give what
+(for example when their memory pool owns the whole device).  It must give what
 mto_compliance_grad gives, call after call, although every call reuses the
 same fixed scratch array inside the library.  This file is collected last so
 that a run stopping at the first failure has run every other test first.
