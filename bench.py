@@ -77,8 +77,9 @@ def parse():
     ap.add_argument("--no-two-load-cases", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (for profiling)")
     ap.add_argument("--sweep-outer", type=int, default=50)
-    ap.add_argument("--study", choices=["levels"], default=None,
-                    help="instead of the bench line: pCGMG level study on the paper's meshes")
+    ap.add_argument("--study", choices=["levels", "configs"], default=None,
+                    help="instead of the bench line: pCGMG level study on the paper's meshes (levels), "
+                         "or one row per single-solve workload: oracle and GPU (configs)")
     ap.add_argument("--study-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--study-outer", type=int, default=500,
                     help="level study: most outer optimiser iterations per mesh and level")
@@ -181,18 +182,18 @@ from synth import dirichlet_design, load_top_edge
 n, nc, max_it, gamma = {n}, {nc}, {max_it}, {gamma}
 x = dirichlet_design(n, n, 4, {seed}); f = load_top_edge(n, n)
 t = {{}}
-r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol=1e-8, max_it=max_it,
+r = solver.solve_pcgmg(n, n, x, {ep!r}, {penal}, f, n_coarsen=nc, tol={tol!r}, max_it=max_it,
                        gamma=gamma, timings=t)
 t.update(iters=r["iters"], converged=bool(r["converged"]), host_cores=os.cpu_count())
 print(json.dumps(t))
 """
 
 
-def oracle_run(n, nc, max_it, gamma=1):
+def oracle_run(n, nc, max_it, gamma=1, tol=1e-8):
     """One oracle pCGMG solve (1 thread) in a subprocess, stopped after max_it
     PCG iterations; returns its set-up, start and per-iteration wall times."""
     code = ORACLE_SNIPPET.format(root=ROOT, n=n, nc=nc, max_it=max_it, seed=SEED, ep=EP, penal=PENAL,
-                                 gamma=gamma)
+                                 gamma=gamma, tol=tol)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
@@ -760,10 +761,91 @@ def run_level_study(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Per-workload table: the single-solve workloads (64^2 to 1e-10 with three
+# grids; 256^2, 512^2, 1024^2 with 4-6 coarsenings; 2048^2 with 7), each
+# timed on the GPU in both precisions and as one full oracle solve on one
+# host core, in the same run.
+# ---------------------------------------------------------------------------
+CONFIG_ROWS = ((64, 2, 1e-10), (256, 4, 1e-8), (512, 5, 1e-8), (1024, 6, 1e-8), (2048, 7, 1e-8))
+
+
+def run_config_study(args):
+    """One JSON line per workload: per precision the median device time of
+    set_design + cold solve + compliance and sensitivities over args.steps
+    steps (after args.warmup), PCG iterations, float64 true residual,
+    GDOF-iterations/s, and the K p and first-smoothing kernels' times with
+    their HBM (and float64-pipe) fractions; then one full oracle solve."""
+    import torch
+
+    from paper_2301_07457_gb300.build import build
+    build()
+    import paper_2301_07457_gb300 as mto
+    from synth import dirichlet_design, load_top_edge
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    hbm_peak, peak_kind = peaks()
+    fp64_peak = mto.measure_fp64_rate(0)
+    for n, nc, tol in CONFIG_ROWS:
+        x = torch.from_numpy(dirichlet_design(n, n, 4, SEED)).to(dev)
+        f = torch.from_numpy(load_top_edge(n, n)).to(dev)
+        nodes = (n + 1) * (n + 1)
+        row = {"study": "configs", "mesh": f"{n}x{n}", "dofs": ndof(n), "n_coarsen": nc, "tol": tol,
+               "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind, "fp64_peak_ops": fp64_peak}
+        for prec in ("fp64", "mixed"):
+            mesh = mto.Mesh(n, n, n_coarsen=nc, precision=prec, tol=tol, max_it=1000, device=0)
+            mesh.set_design(x, EP, PENAL)
+            mesh.autotune()
+
+            def step():
+                mesh.set_design(x, EP, PENAL)
+                u, st = mesh.solve(f)
+                mesh.compliance_grad(f, u)
+                return st
+
+            ms = []
+            for rep in range(args.warmup + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = step()
+                e1.record()
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+            med = sorted(ms)[len(ms) // 2]
+            mesh.set_kernel_timing(True)
+            step()
+            mesh.set_kernel_timing(True)
+            step()
+            (kp_ms, sm_ms), _ = mesh.kernel_times()
+            mesh.set_kernel_timing(False)
+            kp_bytes = KP_BYTES_PER_NODE[prec] * nodes
+            sm_bytes = (SMOOTH64_BYTES_PER_NODE if prec == "fp64" else SMOOTH32_BYTES_PER_NODE) * nodes
+            row[prec] = {"ms_step": med, "ms_solve": st["ms_solve"], "iters": st["iters"],
+                         "rel_res_true": st["rel_res_true"],
+                         "gdof_iter_s": ndof(n) * st["iters"] / (med / 1000.0) / 1e9,
+                         "kp_ms": kp_ms, "kp_frac_hbm": kp_bytes / (kp_ms / 1000.0) / 1e9 / hbm_peak,
+                         "kp_frac_fp64": KP_OPS_PER_NODE * nodes / (kp_ms / 1000.0) / fp64_peak,
+                         "smooth_ms": sm_ms,
+                         "smooth_frac_hbm": sm_bytes / (sm_ms / 1000.0) / 1e9 / hbm_peak}
+            if prec == "fp64":
+                row[prec]["smooth_frac_fp64"] = SMOOTH64_OPS_PER_NODE * nodes / (sm_ms / 1000.0) / fp64_peak
+            mesh.close()
+        d = oracle_run(n, nc, 1000, tol=tol)
+        row["oracle"] = {"threads": 1, "host_cores": d["host_cores"], "iters": d["iters"],
+                         "converged": d["converged"], "s_setup": d["setup_s"],
+                         "s_total": d["setup_s"] + d["start_s"] + sum(d["iter_s"])}
+        print(json.dumps(row), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.study == "levels":
         return run_level_study(args)
+    if args.study == "configs":
+        return run_config_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
