@@ -286,6 +286,9 @@ def run_batched(mto, dev, local):
     t0 = time.perf_counter()
     batch = mto.Batch(problems)
     build_ms = 1000 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    tuned_w = batch.tune()
+    tune_ms = 1000 * (time.perf_counter() - t0)
     def cold_run():
         for pr in batch.problems:
             pr["u"].zero_()  # every run solves from u = 0
@@ -304,6 +307,7 @@ def run_batched(mto, dev, local):
            "ms_per_batch": ms, "load_cases_per_s": 2 * len(problems) / (ms / 1000.0),
            "gdof_iter_s": dof_iters / (ms / 1000.0) / 1e9, "iters_total": iters,
            "all_converged": all(s["converged"] == 1 for s in st), "graph_build_ms": build_ms,
+           "batch_tune": {"warps_per_sm": tuned_w, "ms": tune_ms},
            "max_rel_res_true": max(s["rel_res_true"] for s in st)}
     batch.close()
     for pr in problems:

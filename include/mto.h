@@ -169,6 +169,19 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
                             void* cuda_stream);
 mto_status mto_batch_run(mto_batch* batch, mto_solve_stats* stats);
 mto_status mto_batch_time(mto_batch* batch, double* ms_last_run);
+/* Launch shapes for the batch as a whole: the problems run side by side, so
+ * launches sized for one problem alone (one full wave of blocks per sweep)
+ * hold SMs that the other problems' kernels could use.  Times the batch graph
+ * with each context's own launch shapes and with one cap of 16, 8, 6, 4, 3
+ * or 2 warps per SM on every sweep of every problem (two cold runs each, from
+ * u = 0; the u_dev contents at the call are put back), recaptures the graph
+ * with the fastest and reports its cap in *warps_per_sm (0: the contexts' own
+ * shapes; may be NULL).  The contexts keep their own shapes for their own
+ * solves.  The runs overwrite the items' compliance and dcdx arrays; results
+ * with another shape differ from the untuned batch only in the order of the
+ * reductions' partial sums.  On an error other than MTO_ERR_OOM the batch
+ * must be destroyed.  Takes about 15 batch runs. */
+mto_status mto_batch_tune(mto_batch* batch, int* warps_per_sm);
 void mto_batch_destroy(mto_batch* batch);
 mto_status mto_solve_batched(int n, mto_ctx* const* ctxs, const mto_batch_item* items,
                              mto_solve_stats* stats, void* cuda_stream);

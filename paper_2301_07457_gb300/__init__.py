@@ -360,6 +360,15 @@ class Batch:
         _lib.check(self._lib.mto_batch_time(self._h, ctypes.byref(v)), "mto_batch_time")
         return v.value
 
+    def tune(self):
+        """Launch shapes for the batch as a whole (mto_batch_tune, timed on cold
+        solves); returns the chosen cap in warps per SM (0: each mesh's own
+        shapes).  The problems' u tensors keep their contents."""
+        w = ctypes.c_int()
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.mto_batch_tune(self._h, ctypes.byref(w)), "mto_batch_tune")
+        return w.value
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._lib.mto_batch_destroy(self._h)

@@ -122,6 +122,7 @@ SIGNATURES = {
     "mto_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                         ctypes.POINTER(BatchItem), _P]),
     "mto_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(SolveStats)]),
+    "mto_batch_tune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "mto_batch_time": (ctypes.c_int, [_P, _D]),
     "mto_batch_destroy": (None, [_P]),
     "mto_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(BatchItem),

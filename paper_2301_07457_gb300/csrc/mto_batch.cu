@@ -101,6 +101,65 @@ long long slot_launches(const mto_ctx* c) {
   return n;
 }
 
+// (Re)captures the batch graph with the contexts' current launch shapes.
+mto_status capture_batch(mto_batch* b) {
+  const int n = (int)b->ctx.size();
+  if (b->exec) {
+    CK(cudaStreamSynchronize(b->origin));
+    CK(cudaGraphExecDestroy(b->exec));
+    b->exec = nullptr;
+  }
+  // Workspaces for the load cases of each problem (allocated before the
+  // capture: allocation is not allowed while capturing).
+  std::vector<int> slots(n, 1);
+  for (int i = 0; i < n; ++i) {
+    ST(grow_design(b->ctx[i], b->items[i].n_phase));
+    ST(ensure_slots(b->ctx[i], std::min(b->items[i].n_rhs, b->ctx[i]->o.concurrent_rhs), &slots[i]));
+    CK(cudaStreamSynchronize(b->ctx[i]->stream));
+  }
+  // Capture: fork from the origin stream to every context's stream, join back.
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+  mto_status st = MTO_OK;
+  long long fixed = 0;
+  g_pdl = false;  // concurrent branches: no early-waiting blocks (see launch_pdl)
+  cudaError_t ce = cudaEventRecord(b->fork, b->origin);
+  for (int i = 0; i < n && st == MTO_OK && ce == cudaSuccess; ++i) {
+    mto_ctx* c = b->ctx[i];
+    ce = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    if (ce != cudaSuccess) break;
+    const long long before = c->launches, before_w = slot_launches(c);
+    st = capture_branch(c, b->items[i], b->E_phase[i].data(), slots[i]);
+    fixed += c->launches - before + slot_launches(c) - before_w;
+    c->launches = before;
+    for (mto_ctx* w : c->slots) w->launches = 0;
+    if (st == MTO_OK) ce = cudaEventRecord(b->join[i], c->stream);
+    if (st == MTO_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+  }
+  const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+  g_pdl = true;
+  for (mto_ctx* c : b->ctx) {
+    c->cs = c->stream;
+    for (mto_ctx* w : c->slots) w->cs = w->stream;
+  }
+  if (st != MTO_OK || ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != MTO_OK) return st;
+    g_last_cuda = ce != cudaSuccess ? ce : ee;
+    return MTO_ERR_CUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    b->exec = nullptr;
+    g_last_cuda = ie;
+    return MTO_ERR_CUDA;
+  }
+  b->fixed_kernels = fixed;
+  return MTO_OK;
+}
+
 // Launch shapes already measured in this process: (nx, ny, float32?, source,
 // SM count) -> best target warps.
 std::mutex g_tune_mutex;
@@ -159,55 +218,9 @@ mto_status mto_batch_create(mto_batch** out, int n, mto_ctx* const* ctxs, const 
   BK(cudaEventCreate(&b->ev_b));
   b->join.resize(n, nullptr);
   for (int i = 0; i < n; ++i) BK(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
-  // Workspaces for the load cases of each problem (allocated before the
-  // capture: allocation is not allowed while capturing).
-  std::vector<int> slots(n, 1);
-  for (int i = 0; i < n; ++i) {
-    mto_status s = grow_design(b->ctx[i], items[i].n_phase);
-    if (s == MTO_OK)
-      s = ensure_slots(b->ctx[i], std::min(items[i].n_rhs, b->ctx[i]->o.concurrent_rhs), &slots[i]);
-    if (s != MTO_OK) return fail(s);
-    BK(cudaStreamSynchronize(b->ctx[i]->stream));
-  }
-  // Capture: fork from the origin stream to every context's stream, join back.
-  cudaGraph_t graph = nullptr;
-  BK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
-  mto_status st = MTO_OK;
-  long long fixed = 0;
-  g_pdl = false;  // concurrent branches: no early-waiting blocks (see launch_pdl)
-  cudaError_t ce = cudaEventRecord(b->fork, b->origin);
-  for (int i = 0; i < n && st == MTO_OK && ce == cudaSuccess; ++i) {
-    mto_ctx* c = b->ctx[i];
-    ce = cudaStreamWaitEvent(c->stream, b->fork, 0);
-    if (ce != cudaSuccess) break;
-    const long long before = c->launches, before_w = slot_launches(c);
-    st = capture_branch(c, b->items[i], b->E_phase[i].data(), slots[i]);
-    fixed += c->launches - before + slot_launches(c) - before_w;
-    c->launches = before;
-    for (mto_ctx* w : c->slots) w->launches = 0;
-    if (st == MTO_OK) ce = cudaEventRecord(b->join[i], c->stream);
-    if (st == MTO_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[i], 0);
-  }
-  const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
-  g_pdl = true;
-  for (mto_ctx* c : b->ctx) {
-    c->cs = c->stream;
-    for (mto_ctx* w : c->slots) w->cs = w->stream;
-  }
-  if (st != MTO_OK || ce != cudaSuccess || ee != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    if (st == MTO_OK) g_last_cuda = ce != cudaSuccess ? ce : ee;
-    return fail(st != MTO_OK ? st : MTO_ERR_CUDA);
-  }
-  const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ie != cudaSuccess) {
-    b->exec = nullptr;
-    g_last_cuda = ie;
-    return fail(MTO_ERR_CUDA);
-  }
-  b->fixed_kernels = fixed;
 #undef BK
+  const mto_status cs = capture_batch(b);
+  if (cs != MTO_OK) return fail(cs);
   *out = b;
   return MTO_OK;
 }
@@ -276,6 +289,97 @@ mto_status mto_solve_batched(int n, mto_ctx* const* ctxs, const mto_batch_item* 
 mto_status mto_batch_time(mto_batch* b, double* ms) {
   if (!b || !ms) return MTO_ERR_ARG;
   *ms = b->ms_last;
+  return MTO_OK;
+}
+
+mto_status mto_batch_tune(mto_batch* b, int* warps_per_sm) {
+  NvtxRange nvtx_range("mto_batch_tune");
+  if (!b) return MTO_ERR_ARG;
+  CK(cudaSetDevice(b->device));
+  const int n = (int)b->ctx.size();
+  // The trial runs are cold solves (from u = 0); the caller's u is saved and
+  // put back at the end.
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const mto_ctx* c = b->ctx[i];
+    off[i + 1] = off[i] + (size_t)b->items[i].n_rhs * 2 * (c->nelx + 1) * (c->nely + 1);
+  }
+  double* saved = nullptr;
+  if (device_alloc(reinterpret_cast<void**>(&saved), off[n] * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return MTO_ERR_OOM;
+  }
+  CK(cudaEventRecord(b->ev_in, b->user_stream));
+  CK(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+  // mode 0: save u, 1: restore it, 2: zero it.
+  auto copy_u = [&](int mode) -> cudaError_t {
+    for (int i = 0; i < n; ++i) {
+      double* u = b->items[i].u_dev;
+      const size_t bytes = (off[i + 1] - off[i]) * sizeof(double);
+      const cudaError_t e =
+          mode == 0 ? cudaMemcpyAsync(saved + off[i], u, bytes, cudaMemcpyDeviceToDevice, b->origin)
+          : mode == 1 ? cudaMemcpyAsync(u, saved + off[i], bytes, cudaMemcpyDeviceToDevice, b->origin)
+                      : cudaMemsetAsync(u, 0, bytes, b->origin);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // The contexts' own launch shapes (candidate -1) and a shared cap of W
+  // warps per SM on every sweep of every problem: side by side, smaller
+  // launches of each problem leave SMs to the other problems' kernels.
+  std::vector<std::vector<int>> own(n);
+  for (int i = 0; i < n; ++i) {
+    own[i].assign(b->ctx[i]->tw, b->ctx[i]->tw + MAX_LEVELS);
+    own[i].push_back(b->ctx[i]->tw64);
+  }
+  auto set_shapes = [&](int W) {
+    for (int i = 0; i < n; ++i) {
+      mto_ctx* c = b->ctx[i];
+      for (int l = 0; l < MAX_LEVELS; ++l) c->tw[l] = W < 0 ? own[i][l] : W * c->num_sms;
+      c->tw64 = W < 0 ? own[i][MAX_LEVELS] : W * c->num_sms;
+      invalidate_graphs(c);
+    }
+  };
+  mto_status st = MTO_OK;
+  cudaError_t ce = copy_u(0);
+  const int cand[] = {-1, 16, 8, 6, 4, 3, 2};
+  int best = -1;
+  float best_ms = 0.f;
+  for (int W : cand) {
+    if (st != MTO_OK || ce != cudaSuccess) break;
+    set_shapes(W);
+    st = capture_batch(b);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && st == MTO_OK && ce == cudaSuccess; ++rep) {
+      ce = copy_u(2);
+      if (ce == cudaSuccess) ce = cudaEventRecord(b->ev_a, b->origin);
+      if (ce == cudaSuccess) ce = cudaGraphLaunch(b->exec, b->origin);
+      if (ce == cudaSuccess) ce = cudaEventRecord(b->ev_b, b->origin);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(b->ev_b);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, b->ev_a, b->ev_b);
+    }
+    if (st == MTO_OK && ce == cudaSuccess && (best_ms == 0.f || ms < best_ms)) {
+      best = W;
+      best_ms = ms;
+    }
+  }
+  // Keep the fastest; the contexts get their own shapes back (their own
+  // solve graphs are rebuilt on their next solve).
+  if (st == MTO_OK && ce == cudaSuccess) {
+    set_shapes(best);
+    st = capture_batch(b);
+  }
+  if (ce == cudaSuccess) ce = copy_u(1);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->origin);
+  set_shapes(-1);
+  device_free(saved);
+  if (ce != cudaSuccess) {
+    g_last_cuda = ce;
+    return MTO_ERR_CUDA;
+  }
+  ST(st);
+  b->ms_last = best_ms;
+  if (warps_per_sm) *warps_per_sm = best < 0 ? 0 : best;
   return MTO_OK;
 }
 

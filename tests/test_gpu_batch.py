@@ -126,3 +126,47 @@ def test_autotune_keeps_results(mto, prec):
     assert abs(s1["iters"] - s0["iters"]) <= 1
     assert (u1 - u0).norm().item() <= 1e-6 * u0.norm().item()
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_tune(mto, prec):
+    # mto_batch_tune times shared launch-shape caps over the whole batch and
+    # recaptures its graph with the fastest: the answers change only in the
+    # order of partial sums, the caller's u comes back unchanged, and each
+    # mesh keeps its own shapes for its own solves.
+    sizes = [(64, 64, 2), (128, 64, 3), (256, 256, 4), (256, 128, 4)]
+    tol = 1e-10 if prec == "fp64" else 1e-8
+    problems, own = [], []
+    for k, (nx, ny, nc) in enumerate(sizes):
+        x = to_dev(dirichlet_design(nx, ny, 4, seed=200 + k))
+        F = to_dev(np.stack([load_top_edge(nx, ny), load_right_edge(nx, ny)]))
+        m = mto.Mesh(nx, ny, n_coarsen=nc, precision=prec, tol=tol)
+        m.set_design(x, EP, 3.0)
+        own.append((m.solve(F)[0], [m.launch_shape(l) for l in range(-1, nc + 1)]))
+        problems.append({"mesh": m, "x": x, "E_phase": EP, "penal": 3.0, "f": F})
+    batch = mto.Batch(problems)
+    for pr in batch.problems:
+        pr["u"].zero_()
+    st0 = batch.run()
+    U0 = [pr["u"].clone() for pr in batch.problems]
+    for pr, u in zip(batch.problems, U0):
+        pr["u"].copy_(0.5 * u)  # a warm start that the tuner must leave in place
+    w = batch.tune()
+    assert w in (0, 16, 8, 6, 4, 3, 2)
+    for pr, u in zip(batch.problems, U0):
+        assert torch.equal(pr["u"], 0.5 * u)
+    for pr in batch.problems:
+        pr["u"].zero_()
+    st1 = batch.run()
+    for pr, u0, a, b in zip(batch.problems, U0, st0, st1):
+        assert b["converged"] == 1 and abs(a["iters"] - b["iters"]) <= 1
+        assert (pr["u"] - u0).norm().item() <= 1e-6 * u0.norm().item()
+    # Each mesh's own solve: its own shapes, the same answer as before.
+    for pr, (u_own, shapes) in zip(problems, own):
+        m = pr["mesh"]
+        assert [m.launch_shape(l) for l in range(-1, m.opts.n_coarsen + 1)] == shapes
+        m.set_design(pr["x"], EP, 3.0)
+        assert torch.equal(m.solve(pr["f"])[0], u_own)
+    batch.close()
+    for pr in problems:
+        pr["mesh"].close()
