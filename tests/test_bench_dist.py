@@ -48,6 +48,45 @@ def test_two_ranks_take_the_slowest_time():
     assert value == pytest.approx(2 * 5 / 0.150)
 
 
+def replica_worker(rank, world, port, out):
+    # Each rank solves its own replica of the seeded workload (the CPU oracle
+    # stands in for the device solve); nothing crosses ranks on the data path.
+    # The all_gather below is the test's, to compare the ranks' answers.
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import solver
+    from synth import dirichlet_design, load_top_edge
+    n = 32
+    x, f = dirichlet_design(n, n, 4, 0), load_top_edge(n, n)
+    r = solver.solve_pcgmg(n, n, x, [1.0, 0.5, 0.25, 1e-9], 3.0, f, n_coarsen=2, tol=1e-10)
+    mine = torch.tensor([float(f.ravel() @ r["u"].ravel()), float(r["iters"])], dtype=torch.float64)
+    got = [torch.zeros(2, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(got, mine)
+    out[rank] = [tuple(g.tolist()) for g in got]
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_solve_identical_replicas():
+    port = free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(replica_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    assert out[0] == out[1]
+    (c0, it0), (c1, it1) = out[0]
+    assert c0 == c1 and it0 == it1
+    # The same answer as one process alone.
+    sys.path.insert(0, ROOT)
+    from oracle import solver
+    from synth import dirichlet_design, load_top_edge
+    n = 32
+    x, f = dirichlet_design(n, n, 4, 0), load_top_edge(n, n)
+    r = solver.solve_pcgmg(n, n, x, [1.0, 0.5, 0.25, 1e-9], 3.0, f, n_coarsen=2, tol=1e-10)
+    assert c0 == float(f.ravel() @ r["u"].ravel()) and it0 == r["iters"]
+
+
 def test_single_rank_needs_no_process_group():
     sys.path.insert(0, ROOT)
     import bench
