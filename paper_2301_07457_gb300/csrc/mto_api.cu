@@ -1379,18 +1379,22 @@ mto_status mto_run_host(mto_ctx* c, int n_phase, const double* x_host, const dou
   return s;
 }
 
+// Streams, pinned records and events of the pipelined host calls, created on
+// first use (what an earlier failed attempt already created is kept; all of
+// it is released by mto_destroy).
 static mto_status hq_setup(mto_ctx* c) {
   if (c->hq_ready) return MTO_OK;
-  CK(cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking));
+  if (!c->down) CK(cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking));
   for (HostCall& h : c->hq) {
-    CK(cudaMallocHost(&h.stats, sizeof(RhsStats) * MAX_RHS));
-    CK(cudaMallocHost(&h.err, sizeof(int)));
-    for (cudaEvent_t* e : {&h.setup0, &h.setup1, &h.t0, &h.t1}) CK(cudaEventCreate(e));
-    CK(cudaEventCreateWithFlags(&h.in, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
+    if (!h.stats) CK(cudaMallocHost(&h.stats, sizeof(RhsStats) * MAX_RHS));
+    if (!h.err) CK(cudaMallocHost(&h.err, sizeof(int)));
+    for (cudaEvent_t* e : {&h.setup0, &h.setup1, &h.t0, &h.t1})
+      if (!*e) CK(cudaEventCreate(e));
+    for (cudaEvent_t* e : {&h.in, &h.done})
+      if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
   for (cudaEvent_t* e : {&c->ev_stage_free[0], &c->ev_stage_free[1], &c->ev_u_out, &c->ev_g_out, &c->ev_cmp})
-    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   c->hq_ready = true;
   return MTO_OK;
 }

@@ -49,6 +49,7 @@ def random_nodal(nx, ny, fixed, seed):
 
 MESHES = [
     (64, 64, 3, BOTTOM),        # the 64x64 square wall
+    (64, 64, 2, BOTTOM),        # the same with three grids (down to 16 x 16)
     (200, 136, 3, BOTTOM),      # several strips and chunks, ragged in both directions
     (96, 40, 2, BOTTOM | LEFT),
     (48, 80, 4, BOTTOM | RIGHT | TOP),
