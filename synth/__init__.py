@@ -19,6 +19,7 @@ from .designs import (  # noqa: F401
     TOP,
     batch_sizes,
     dirichlet_design,
+    dirichlet_design_torch,
     load_right_edge,
     load_top_edge,
     splitmix64,

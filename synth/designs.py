@@ -58,6 +58,38 @@ def dirichlet_design(nelx, nely, n_phase, seed, chunk=1 << 22):
     return out.reshape(n_phase, nely, nelx)
 
 
+def _signed64(v):
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def dirichlet_design_torch(nelx, nely, n_phase, seed, device, chunk=1 << 22):
+    """dirichlet_design computed with torch on `device` (for designs too large
+    to build on the host): the same counters and the same 53-bit variates,
+    with the uint64 arithmetic done in int64 (products and sums wrap modulo
+    2^64 alike; right shifts are made logical by masking).  The logarithm is
+    torch's, so fractions may differ from the numpy version in the last bit."""
+    import torch
+
+    g_inc, m1, m2 = (_signed64(int(v)) for v in (_GAMMA, _M1, _M2))
+
+    def lsr(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    n_el = nelx * nely
+    out = torch.empty((n_phase, n_el), dtype=torch.float64, device=device)
+    ph = torch.arange(n_phase, dtype=torch.int64, device=device)[:, None]
+    for s in range(0, n_el, chunk):
+        e = torch.arange(s, min(n_el, s + chunk), dtype=torch.int64, device=device)
+        z = (e[None, :] * n_phase + ph) ^ seed
+        z = z + g_inc
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        g = -torch.log((lsr(z, 11).to(torch.float64) + 1.0) * 2.0**-53)
+        out[:, s:s + e.numel()] = g / g.sum(dim=0, keepdim=True)
+    return out.reshape(n_phase, nely, nelx)
+
+
 def batch_sizes(n, seed, choices=(128, 256, 512, 1024)):
     """n square mesh sizes drawn uniformly from `choices` by the counter-based generator."""
     u = uniform01(seed, np.arange(n, dtype=np.uint64))

@@ -33,3 +33,18 @@ def test_loads():
     assert f.shape == (4, 5, 2) and f[3, :, 1].sum() == -5 and np.count_nonzero(f) == 5
     g = load_right_edge(4, 3)
     assert g[:, 4, 0].sum() == 4 and np.count_nonzero(g) == 4
+
+
+def test_torch_generator_matches_numpy():
+    # The device version of the design generator (for designs too large to
+    # build on the host), run here on CPU tensors: the same fractions up to
+    # the rounding of the logarithm and of the normalising sum (a few ulps;
+    # a wrong bit in the integer hash would change a fraction by O(1)), for
+    # several phase counts, chunkings and seeds, including seeds above 2^63.
+    import torch
+    from synth import dirichlet_design_torch
+    for nelx, nely, n_phase, seed, chunk in ((33, 17, 4, 0, 1 << 22), (40, 24, 16, 9, 100),
+                                            (16, 8, 3, (1 << 63) + 12345, 7)):
+        ref = dirichlet_design(nelx, nely, n_phase, seed)
+        got = dirichlet_design_torch(nelx, nely, n_phase, seed, torch.device("cpu"), chunk=chunk).numpy()
+        np.testing.assert_allclose(got, ref, rtol=2e-15, atol=0)
