@@ -52,7 +52,8 @@ typedef struct mto_ctx mto_ctx; /* opaque; owned by the library */
 typedef enum {
   MTO_OK = 0,
   MTO_ERR_ARG = 1,              /* invalid argument (null pointer, bad size, bad option) */
-  MTO_ERR_UNSUPPORTED_MESH = 2, /* nelx or nely not divisible by 2^n_coarsen, coarsest grid too large */
+  MTO_ERR_UNSUPPORTED_MESH = 2, /* nelx or nely not divisible by 2^n_coarsen, coarsest grid too large,
+                                   more than 2^30 elements */
   MTO_ERR_OOM = 3,              /* device allocation failed */
   MTO_ERR_CUDA = 4,             /* a CUDA call failed */
   MTO_ERR_NOT_CONVERGED = 5,    /* max_it reached; u holds the last iterate */
@@ -110,7 +111,8 @@ void mto_default_opts(mto_solver_opts* opts);
 /* Creates a context for an nelx x nely mesh with Poisson ratio nu and the
  * given clamped edges (at least one, so that K_ff is positive definite).
  * Allocates every device buffer of the level hierarchy (sizes depend only on
- * the mesh and the options).  device: CUDA ordinal; cuda_stream: a
+ * the mesh and the options).  Meshes of more than 2^30 elements are
+ * rejected with MTO_ERR_UNSUPPORTED_MESH before any allocation.  device: CUDA ordinal; cuda_stream: a
  * cudaStream_t (NULL = legacy default stream).
  * Paper: Eq. 6-10 (problem statement), Alg. 1 (grid hierarchy). */
 mto_status mto_create_mesh(mto_ctx** out, int nelx, int nely, double nu, unsigned fixed_edges,

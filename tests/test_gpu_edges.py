@@ -115,6 +115,9 @@ def test_mesh_limits(mto):
     with pytest.raises(MtoError) as e:
         mto.Mesh(100, 64, n_coarsen=3)
     assert e.value.code == _lib.ERR_UNSUPPORTED_MESH
+    with pytest.raises(MtoError) as e:  # 2^31 elements: above the 2^30 cap, rejected before allocating
+        mto.Mesh(65536, 32768, n_coarsen=11)
+    assert e.value.code == _lib.ERR_UNSUPPORTED_MESH
     m = mto.Mesh(64, 64, n_coarsen=1)  # coarsest 32 x 32: 2112 free DOFs, band Cholesky in global memory
     x = dirichlet_design(64, 64, 4, seed=9)
     f = load_top_edge(64, 64)
