@@ -172,3 +172,26 @@ def test_guard_zones_pinned(mto):
         assert np.array_equal(b["C"][0][G:G + 2].numpy(), C_ref)
         assert np.array_equal(b["g"][0][G:G + x.size].numpy(), g_ref.ravel())
     m.close()
+
+
+def test_breakdown_in_flight(mto):
+    # A design whose coarsest system cannot be factorised (a NaN fraction)
+    # between two good calls: its wait reports the breakdown, the calls
+    # around it are unaffected, and the context keeps working.
+    from paper_2301_07457_gb300 import MtoError, _lib
+    nelx, nely = 96, 64
+    m = mto.Mesh(nelx, nely, n_coarsen=3, precision="mixed")
+    x, f = dirichlet_design(nelx, nely, 4, seed=11), load_top_edge(nelx, nely)
+    r = m.run_host(x, EP, 3.0, f)
+    bad = x.copy()
+    bad[0, 7, 9] = np.nan
+    m.run_host_async(x, EP, 3.0, f)
+    m.run_host_async(bad, EP, 3.0, f)
+    same(m.run_host_wait(), r)
+    with pytest.raises(MtoError) as e:
+        m.run_host_wait()
+    assert e.value.code == _lib.ERR_BREAKDOWN
+    m.run_host_async(x, EP, 3.0, f)
+    same(m.run_host_wait(), r)
+    same(m.run_host(x, EP, 3.0, f), r)
+    m.close()
