@@ -49,8 +49,8 @@ SMOOTH64_BYTES_PER_NODE = 48
 # DRAM bytes per launch at 2048^2 from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/sweeps_2048_ncu_full.md); None once the
 # kernel changes.
-KP_TRAFFIC = 354_025_984
-SMOOTH32_TRAFFIC = 249_000_704
+KP_TRAFFIC = 354_211_328
+SMOOTH32_TRAFFIC = 249_079_296
 # Nominal float64 pipe rate, for context next to the measured one: 2
 # operations per clock per SM (1.25 TFLOP/s at 2 flops per FMA), 152 SMs,
 # 2070 MHz.
