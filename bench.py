@@ -46,9 +46,9 @@ KP_BYTES_PER_NODE = {"mixed": 96, "fp64": 104}
 SMOOTH32_BYTES_PER_NODE = 66
 SMOOTH64_OPS_PER_NODE = 38
 SMOOTH64_BYTES_PER_NODE = 48
-# DRAM bytes per launch at 2048^2 from one ncu --set full capture of each
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum, the launch after the
-# warm-up step); to be set to None whenever the kernel changes.
+# DRAM bytes per launch at 2048^2 from an ncu --set full capture of one
+# launch of each kernel in this bench's step (dram__bytes_read.sum +
+# dram__bytes_write.sum); to be set to None whenever the kernel changes.
 KP_TRAFFIC = 354_211_328
 SMOOTH32_TRAFFIC = 249_079_296
 # Nominal float64 pipe rate, for context next to the measured one: 2
