@@ -598,21 +598,28 @@ def run_ours(args):
 
         host_step()
         pipelined(2)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            host_step()
-        t_block = max_over_ranks_here(time.perf_counter() - t0)
-        barrier()
-        t0 = time.perf_counter()
-        pipelined(args.steps)
-        t_e2e = max_over_ranks_here(time.perf_counter() - t0)
+        # Wall-clock over at least 20 steps, three times each: one host-side
+        # stall weighs on a short loop, and the median of three repeats
+        # keeps the number to what the path sustains.
+        e2e_steps = max(args.steps, 20)
+        blocking_vals, pipelined_vals = [], []
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                host_step()
+            blocking_vals.append(world * e2e_steps / max_over_ranks_here(time.perf_counter() - t0))
+            barrier()
+            t0 = time.perf_counter()
+            pipelined(e2e_steps)
+            pipelined_vals.append(world * e2e_steps / max_over_ranks_here(time.perf_counter() - t0))
         b = sets[0]
-        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+        e2e = {"value": sorted(pipelined_vals)[1], "unit": UNIT,
                "h2d_bytes_per_step": b["x"].numel() * 8 + b["f"].numel() * 8,
                "d2h_bytes_per_step": b["u"].numel() * 8 + b["g"].numel() * 8 + 8,
                "api": "mto_run_host_async + mto_run_host_wait, two steps in flight",
-               "blocking_value": world * args.steps / t_block}
+               "steps": e2e_steps, "repeats": pipelined_vals,
+               "blocking_value": sorted(blocking_vals)[1], "blocking_repeats": blocking_vals}
 
     # FP64 path on the same input.
     fp64 = None
