@@ -1414,9 +1414,14 @@ mto_status mto_run_host_async(mto_ctx* c, int n_phase, const double* x_host, con
   const int slot = (c->hq_head + c->hq_count) & 1;
   HostCall& h = c->hq[slot];
   // Buffers (grown ones keep their old allocation alive for a call in flight).
+  // Both staging areas grow together, so that the allocation, which can wait
+  // for the device, happens before this call enqueues anything rather than
+  // behind the previous call's kernels.
   ST(grow(c, &c->xdes, &c->xdes_cap, (size_t)n_phase * nel));
-  ST(grow(c, &c->xstage[slot], &c->xstage_cap[slot], (size_t)n_phase * nel));
-  ST(grow(c, &c->fstage[slot], &c->fstage_cap[slot], (size_t)n_rhs * nd));
+  for (int s = 0; s < 2; ++s) {
+    ST(grow(c, &c->xstage[s], &c->xstage_cap[s], (size_t)n_phase * nel));
+    ST(grow(c, &c->fstage[s], &c->fstage_cap[s], (size_t)n_rhs * nd));
+  }
   ST(grow(c, &c->hu, &c->hu_cap, (size_t)n_rhs * nd));
   size_t ccap = (size_t)c->hc_cap;
   ST(grow(c, &c->hc, &ccap, (size_t)n_rhs));
