@@ -603,23 +603,25 @@ def run_ours(args):
         # keeps the number to what the path sustains.
         e2e_steps = max(args.steps, 20)
         blocking_vals, pipelined_vals = [], []
-        for _ in range(3):
-            barrier()
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                host_step()
-            blocking_vals.append(world * e2e_steps / max_over_ranks_here(time.perf_counter() - t0))
-            barrier()
-            t0 = time.perf_counter()
-            pipelined(e2e_steps)
-            pipelined_vals.append(world * e2e_steps / max_over_ranks_here(time.perf_counter() - t0))
+        with ClockSampler(local) as clk_e2e:
+            for _ in range(3):
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(e2e_steps):
+                    host_step()
+                blocking_vals.append(world * e2e_steps / max_over_ranks_here(time.perf_counter() - t0))
+                barrier()
+                t0 = time.perf_counter()
+                pipelined(e2e_steps)
+                pipelined_vals.append(world * e2e_steps / max_over_ranks_here(time.perf_counter() - t0))
         b = sets[0]
         e2e = {"value": sorted(pipelined_vals)[1], "unit": UNIT,
                "h2d_bytes_per_step": b["x"].numel() * 8 + b["f"].numel() * 8,
                "d2h_bytes_per_step": b["u"].numel() * 8 + b["g"].numel() * 8 + 8,
                "api": "mto_run_host_async + mto_run_host_wait, two steps in flight",
                "steps": e2e_steps, "repeats": pipelined_vals,
-               "blocking_value": sorted(blocking_vals)[1], "blocking_repeats": blocking_vals}
+               "blocking_value": sorted(blocking_vals)[1], "blocking_repeats": blocking_vals,
+               "clocks": clk_e2e.summary()}
 
     # FP64 path on the same input.
     fp64 = None
