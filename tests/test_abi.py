@@ -102,3 +102,17 @@ def test_memory_ledger_needs_no_gpu(libpath):
     assert lib.mto_device_memory_in_use() == 0  # nothing allocated in this process
     lib.mto_set_device_memory_limit(1 << 20)
     lib.mto_set_device_memory_limit(0)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # No CPU fallback: without libmto.so the binding refuses to work, both
+    # when loaded directly and through the public classes.
+    import pytest
+    from paper_2301_07457_gb300 import _lib
+    import paper_2301_07457_gb300 as mto
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libmto.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError, match="libmto.so not found"):
+        _lib.load()
+    with pytest.raises(ImportError, match="libmto.so not found"):
+        mto.Mesh(32, 32, n_coarsen=2)
